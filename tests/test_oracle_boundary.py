@@ -1,0 +1,111 @@
+"""Pins of the oracle's boundary amplitude e(t) (Sec. 2 (a)-(c)).
+
+Each closed form is checked against an independent numerical integration of
+the one-excitation delay equation it solves (tests/dde_reference.py), against
+probability conservation, and against the Markovian limit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from tests import dde_reference as R
+
+PI = math.pi
+
+
+def params(O, **kw):
+    base = dict(nx=64, nt=64, D=40, delta=0.05, gamma=1.0, omega0=PI / 2, k=PI / 2, init_cond=3, alpha=1.0)
+    base.update(kw)
+    return O.Params(**base)
+
+
+TIMES = [0.3, 1.9, 2.5, 4.1, 7.7, 11.9]
+
+
+def test_e1_series_solves_delay_equation(oracle):
+    # Sec. 2 (b): e1(0) = 1, no drive.
+    p = params(oracle, init_cond=2)
+    ev = R.solve(p.a, p.gamma, p.omega0, 12.0, phi=None, e0=1.0)
+    for t in TIMES:
+        assert abs(oracle.e_at(p, t) - ev(t)) < 1e-11
+
+
+@pytest.mark.parametrize("dk,alpha", [(0.0, 1.0), (0.3, 0.7), (-0.8, 1.6), (1.0, 0.5)])
+def test_e0_exponential_solves_delay_equation(oracle, dk, alpha):
+    # Sec. 2 (c) with the exp(-ika) factor; (0, 1) is p = 0 (config-1 physics).
+    p = params(oracle, k=PI / 2 + dk, alpha=alpha)
+    ev = R.solve(p.a, p.gamma, p.omega0, 12.0,
+                 phi=lambda x: R.phi_exp(x, p.k, alpha, p.gamma, p.a))
+    for t in TIMES:
+        assert abs(oracle.e_at(p, t) - ev(t)) < 1e-11
+
+
+def test_e0_without_phase_factor_fails(oracle):
+    # The printed e0 of Sec. 2 (c) without exp(-ika) does not solve the
+    # delay equation: the factor is needed (reading recorded in the design notes).
+    p = params(oracle, k=PI / 2 + 0.3, alpha=0.7)
+    ev = R.solve(p.a, p.gamma, p.omega0, 4.0, phi=lambda x: R.phi_exp(x, p.k, 0.7, p.gamma, p.a))
+    t = 1.3
+    printed = oracle.e_at(p, t) * np.exp(1j * p.k * p.a)
+    assert abs(printed - ev(t)) > 0.1 * abs(ev(t))
+
+
+def test_e0_gaussian_solves_delay_equation(oracle):
+    p = params(oracle, init_cond=4, sigma=1.0, center=-1.0 - 8.0)
+    ev = R.solve(p.a, p.gamma, p.omega0, 24.0,
+                 phi=lambda x: R.phi_gauss(x, p.k, 1.0, -9.0, p.a))
+    for t in TIMES + [17.0, 23.9]:
+        assert abs(oracle.e_at(p, t) - ev(t)) < 1e-11
+
+
+def test_e1_probability_conservation(oracle):
+    # |e|^2 + (Gamma/2) int_{t-2a}^t |e|^2 + (Gamma/2) int_0^t |e(s) - e(s-2a)|^2 = 1:
+    # the atom, the photon between the atom and its image, and the outgoing photon.
+    p = params(oracle, init_cond=2, omega0=1.3)
+    a, G = p.a, p.gamma
+    xg, wg = np.polynomial.legendre.leggauss(30)
+
+    def integ(f, lo, hi):
+        # composite Gauss-Legendre with breakpoints at multiples of 2a
+        pts = [lo] + [b for b in np.arange(0, hi, 2 * a) if lo < b < hi] + [hi]
+        tot = 0.0
+        for u, v in zip(pts[:-1], pts[1:]):
+            for q in range(8):
+                c0, c1 = u + (v - u) * q / 8, u + (v - u) * (q + 1) / 8
+                tot += sum(w * f(0.5 * (c0 + c1) + 0.5 * (c1 - c0) * x) for x, w in zip(xg, wg)) * 0.5 * (c1 - c0)
+        return tot
+
+    e = lambda s: oracle.e_at(p, s) if s >= 0 else 0.0
+    for t in [0.7, 2.6, 5.3]:
+        tot = abs(e(t)) ** 2 + 0.5 * G * integ(lambda s: abs(e(s)) ** 2, max(0.0, t - 2 * a), t) \
+            + 0.5 * G * integ(lambda s: abs(e(s) - e(s - 2 * a)) ** 2, 0.0, t)
+        assert abs(tot - 1.0) < 1e-11
+
+
+def test_e1_markovian_limit(oracle):
+    # Gamma a -> 0 at fixed phase 2 k0 a: e1 -> exp(-[i w0 + (Gamma/2)(1 - exp(2 i w0 a))] t).
+    D = 40
+    a = 1e-3
+    w0 = 0.5 * PI / a  # k0 a = pi/2: decay rate 2 Gamma
+    p = params(oracle, init_cond=2, D=D, delta=2 * a / D, omega0=w0, k=w0)
+    for t in [0.5, 1.0, 2.0]:
+        ref = np.exp(-(1j * w0 + 0.5 * (1 - np.exp(2j * w0 * a))) * t)
+        assert abs(oracle.e_at(p, t) - ref) < 3e-3 * abs(ref)
+
+
+def test_wavepackets_normalised(oracle):
+    # int |phi|^2 dx = 1 for the exponential packet (Sec. 2 (b)); with A = 1/sqrt2
+    # for identical photons (Sec. 2 (c)) the two-photon state is normalised.
+    for ic, kw in [(3, dict(alpha=0.8)), (4, dict(sigma=0.7, center=-1.0 - 5.6))]:
+        p = params(oracle, init_cond=ic, **kw)
+        x = np.linspace(-60.0, -p.a, 200001)
+        f = np.array([abs(oracle.phi(p, v)) ** 2 for v in x[::10]])
+        integral = np.trapezoid(f, x[::10])
+        assert abs(integral - 1.0) < 2e-3
+    k1 = k2 = 0.4
+    a1 = a2 = 0.9
+    Gm = 1.0
+    A = math.sqrt((4 * (k1 - k2) ** 2 + (a1 + a2) ** 2 * Gm ** 2)
+                  / (4 * (k1 - k2) ** 2 + (a1 + a2) ** 2 * Gm ** 2 + 4 * a1 * a2 * Gm ** 2))
+    assert abs(A - 1 / math.sqrt(2)) < 1e-15
