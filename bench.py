@@ -1,0 +1,321 @@
+"""Benchmark of the FDTD march (grid-point updates/s) on GB300.
+
+One step = one pass of the whole path on one instance: plan the boundary
+(e(t) kernel, wavepacket and source tables) and march every row of the
+workload.  Default workload: the large FP64 instance, 2^20 marched columns x
+2^18 rows, D = 2000 (2a = 20/Gamma), k0 a = 0.3 pi, Gaussian pulse sigma =
+5/Gamma.  Its ring of D+2 rows is 33.6 GB, far larger than L2, so no L2 flush
+is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs N independent replicas (one per rank, launched by torchrun); the
+value is the updates of all ranks over the slowest rank's time.  The
+reference arm (--impl reference) times the CPU oracle on a bounded sample of
+the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "grid-point updates/s & % HBM peak; FP32/batched vs plain FP64 at stated error"
+UNIT = "grid-point updates/s"
+# algorithmic work per update of the FP64 bulk (x > 3a):
+#   bytes: one delay value read from HBM + one value written = 2 x 16 B
+#   flops: c1 a (6) + c2 b (6+2) + delay 4-sum (6) x c3 (6+2) + sources (2+6+2+6+2) + c2 y (6+2) = 54
+BYTES_PER_UPDATE_F64 = 32
+FLOPS_PER_UPDATE_F64 = 54
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64 (vector and tensor), NVIDIA's figure
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(w: W.Workload, rows: int, extra_cols: int = 512):
+    """The oracle on a narrow box of the same workload: every column left of
+    max(m, D/2) is exact, so a box of D + extra columns marches the same
+    values the full width would there."""
+    from oracle import oracle as O
+    O.build()
+    nx = min(w.nx, w.D + extra_cols)
+    p = O.Params(nx=nx, nt=rows, D=w.D, delta=w.delta, gamma=w.gamma, omega0=w.omega0, k=w.k,
+                 init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center)
+    t0 = time.perf_counter()
+    O.march(p, rows, tstep=None, norms=True)
+    dt = time.perf_counter() - t0
+    return nx * (rows - 1), dt, nx
+
+
+def run_reference(args, w):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    rows = args.ref_rows
+    for _ in range(args.warmup):
+        oracle_sample(w, max(rows // 8, 8))
+    tot_u, tot_t, nx = 0, 0.0, 0
+    for _ in range(args.steps):
+        u, dt, nx = oracle_sample(w, rows)
+        tot_u += u
+        tot_t += dt
+    v = tot_u / tot_t
+    sample = f"oracle march of {nx} columns x {rows} rows of {w.name} per step (narrow box, FP64, 1 thread)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "nx": w.nx, "nt": w.nt, "D": w.D, "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large", choices=["large", "small"])
+    ap.add_argument("--rows", type=int, default=0, help="march only this many rows (testing)")
+    ap.add_argument("--rows-per-launch", type=int, default=4096)
+    ap.add_argument("--ref-rows", type=int, default=4096)
+    ap.add_argument("--cpu-rows", type=int, default=6144)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    w = W.LARGE if args.workload == "large" else W.SMALL
+    if args.rows:
+        w = w.with_(nt=args.rows, name=f"{w.name}_rows{args.rows}")
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import numpy as np
+    import torch
+
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1707_05943_gb300 import build, fdtd
+    build.build()
+
+    stream = torch.cuda.Stream(device=dev)
+    rpl = args.rows_per_launch
+    cfg = fdtd.Config(nx=w.nx, nt=w.nt, D=w.D, delta=w.delta, gamma=w.gamma, omega0=w.omega0, k=w.k,
+                      init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center, tstep=-1,
+                      rows_per_launch=rpl)
+    solver = fdtd.Solver(cfg, stream=stream)
+    launches_per_step = 5 + math.ceil((w.nt - 1) / rpl)
+
+    def step(events=None):
+        solver.set_boundary()
+        done = 1
+        while done < w.nt:
+            n = min(rpl, w.nt - done)
+            if events is not None:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                solver.march(n)
+                e1.record(stream)
+                events.append((e0, e1, n))
+            else:
+                solver.march(n)
+            done += n
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    norms_w = solver.read(fdtd.READ_NORMS)
+    assert np.all(np.isfinite(norms_w))
+
+    sampler = ClockSampler(local)
+    events = []
+    barrier()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    sampler.start()
+    start.record(stream)
+    for _ in range(args.steps):
+        step(events)
+    stop.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    barrier()
+    ms = start.elapsed_time(stop)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    updates_per_step = w.updates
+    value = world * updates_per_step * args.steps / (ms * 1e-3)
+
+    # dominant kernel: the march launches (full-size ones)
+    full = [(a.elapsed_time(b), n) for a, b, n in events if n == rpl] or [(a.elapsed_time(b), n) for a, b, n in events]
+    avg_ms = sum(t for t, _ in full) / len(full)
+    rows_l = full[0][1]
+    peaks, src = load_peaks()
+    upd_launch = rows_l * w.nx
+    flops_launch = FLOPS_PER_UPDATE_F64 * upd_launch
+    bytes_launch = BYTES_PER_UPDATE_F64 * upd_launch
+    ach_tf = flops_launch / (avg_ms * 1e-3) / 1e12
+    ach_gbs = bytes_launch / (avg_ms * 1e-3) / 1e9
+    roof = {"kernel": "k_march_f64", "bound": "alu", "achieved": ach_tf, "peak": FP64_NOMINAL_TFLOPS,
+            "unit": "TFLOP/s", "frac": ach_tf / FP64_NOMINAL_TFLOPS,
+            "peak_source": "GB300 nominal dense FP64 1.25 TFLOP/s (no FP64 figure in MEASURED_PEAKS.json)",
+            "flops_per_update": FLOPS_PER_UPDATE_F64, "updates_per_launch": upd_launch,
+            "launch_ms": avg_ms, "traffic": None,
+            "hbm": {"achieved": ach_gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                    "frac": ach_gbs / peaks.get("hbm_gbs", 6800.0), "bytes_per_update": BYTES_PER_UPDATE_F64,
+                    "peak_source": src}}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name, "nx": w.nx, "nt": w.nt, "D": w.D, "delta": w.delta,
+                      "k0a": w.omega0 * w.a, "sigma": w.sigma, "precision": "complex128",
+                      "rows_per_launch": rpl, "parallelism": f"replicas x{world}",
+                      "l2": "inputs larger than L2 (ring of D+2 rows = "
+                            f"{(w.D + 2) * w.nx * 16 / 1e9:.1f} GB)"},
+           "roofline": roof, "gpu_launches": launches_per_step * args.steps, "clocks": clocks}
+
+    # end to end through the C ABI with host buffers
+    if not args.no_e2e:
+        pinned_norms = torch.empty(w.nt, dtype=torch.float64, pin_memory=True)
+        pinned_row = torch.empty(2 * w.nx, dtype=torch.float64, pin_memory=True)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            s2 = fdtd.Solver(cfg, stream=stream)
+            s2.set_boundary()
+            s2.march(w.nt)
+            s2.read(fdtd.READ_NORMS, out=pinned_norms)
+            s2.read(fdtd.READ_ROW, out=pinned_row)
+            s2.close()
+            del s2
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        h2d = 8 * (solver_grid(solver) + 1)
+        out["e2e"] = {"value": world * updates_per_step * args.steps / dt, "unit": UNIT,
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * w.nt + 16 * w.nx,
+                      "includes": "plan + workspace allocation + boundary + march + readout of norms and "
+                                  "last row into pinned host memory"}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        u, dt, nx = oracle_sample(w, args.cpu_rows)
+        out["cpu_baseline"] = {"value": u / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"oracle march of {nx} columns x {args.cpu_rows} rows of {w.name} "
+                                         f"({u:.3g} updates, {dt:.1f} s, FP64, 1 thread)"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    solver.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def solver_grid(s) -> int:
+    # column split entries copied host->device by fdtd_set_boundary (grid+1 int64)
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+if __name__ == "__main__":
+    main()

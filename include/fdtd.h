@@ -1,0 +1,190 @@
+/*
+ * fdtd.h -- C ABI of the GB300 (sm_103a) FDTD solver for the 1+1D delay PDE
+ * of waveguide QED: a two-level system at distance a from a mirror, driven by
+ * one or two photons (Fang, "FDTD: solving 1+1D delay PDE in parallel",
+ * arXiv:1707.05943).
+ *
+ * What is computed.  psi(x,t), the amplitude of "atom excited + one photon at
+ * x", obeys Eq. 1: advection, decay W = i w0 + Gamma/2, the delay term
+ * (Gamma/2) psi(x-2a, t-2a), two mirror source terms (lines 2-3) and the
+ * incident two-photon term (line 4).  The library marches Eq. 1 on the square
+ * lattice dx = dt = delta (Sec. 2), with squares (Eq. 3a-c) for line 1 and
+ * bars (Eq. 4) for lines 2-3, in the region x > -a, column by column left to
+ * right and row by row upward.  The exact solution psi(x<=-a,t) = C phi(x-t)
+ * e(t) (Sec. 2 (b),(c)) is the boundary; e(t) involves the incomplete Gamma
+ * function gamma(n,z) (App. C).
+ *
+ * Grid.  Column m is x = m delta, row n is t = n delta, D = 2a/delta (even;
+ * the paper's n_x).  Marched columns are m = -D/2+1 .. -D/2+nx (index
+ * j = m + D/2 - 1 in every buffer below), rows n = 0 .. nt-1.  Row 0 is the
+ * initial condition psi(x>-a, 0) = 0.  Complex values are interleaved
+ * (re, im): complex128 for FDTD_F64, complex64 for FDTD_F32_COMP.
+ *
+ * Memory.  The library never allocates device memory.  fdtd_plan reports the
+ * workspace size; the caller allocates it (any allocator) and lends it with
+ * fdtd_bind_workspace for the plan's lifetime.  The workspace holds a ring of
+ * D+2 rows (the delay term reaches row n-D-1), the boundary tables, the
+ * per-row norms and the optional snapshots.  The library never frees caller
+ * memory.  Host-side plan structs are allocated with malloc and released by
+ * fdtd_destroy.
+ *
+ * Streams and errors.  Every call returns an fdtd_status; nothing throws or
+ * exits.  Work is queued on the plan's stream; fdtd_readout synchronises it.
+ * Device-side failures (a bounded wait that gave up, an index outside a
+ * buffer) latch a status word in the workspace that the next fdtd_readout
+ * returns.  Plans are not thread-safe; use one plan per stream.
+ * Call order: fdtd_plan -> fdtd_bind_workspace -> fdtd_set_boundary ->
+ * fdtd_march* -> fdtd_readout*; out-of-order calls return FDTD_ERR_STATE.
+ */
+#ifndef FDTD_H_
+#define FDTD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fdtd_plan_s* fdtd_plan_t;
+
+typedef enum {
+  FDTD_OK = 0,
+  FDTD_ERR_INVALID_ARG = 1,   /* a parameter is out of range (see fdtd_last_error) */
+  FDTD_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement       */
+  FDTD_ERR_WORKSPACE = 3,     /* workspace missing, too small or misaligned        */
+  FDTD_ERR_CUDA = 4,          /* a CUDA runtime call failed                        */
+  FDTD_ERR_TIMEOUT = 5,       /* a device-side bounded wait gave up                */
+  FDTD_ERR_BOUNDS = 6,        /* a device-side index check failed                  */
+  FDTD_ERR_NOT_CONVERGED = 7, /* a boundary series or quadrature did not converge  */
+  FDTD_ERR_STATE = 8          /* call out of order                                 */
+} fdtd_status;
+
+typedef enum {
+  FDTD_F64 = 0,       /* complex128 march                                          */
+  FDTD_F32_COMP = 1   /* complex64 march with compensated increments; the boundary */
+                      /* tables and the norm reduction stay FP64                   */
+} fdtd_precision;
+
+typedef enum {
+  FDTD_IC_STIM_EMISSION = 2,    /* Sec. 2 (b): atom excited, one exponential photon  */
+  FDTD_IC_TWO_PHOTON_EXP = 3,   /* Sec. 2 (c): two identical exponential photons     */
+  FDTD_IC_TWO_PHOTON_GAUSS = 4  /* two identical Gaussian photons (same structure as  */
+                                /* Sec. 2 (c); e(t) by quadrature, no closed form)    */
+} fdtd_init_cond;
+
+/* Parameters of one instance, in the physical units of the paper's figure
+ * captions (c = 1).  Table 1 keys: Nx (here the number of marched columns,
+ * not the half-width), Ny = nt, nx = D, Delta = delta, k, w0 = omega0, gamma,
+ * init_cond, alpha, Tstep = tstep. */
+typedef struct {
+  uint32_t struct_size;  /* = sizeof(fdtd_params); versions the ABI              */
+  int32_t D;             /* 2a/delta: even, 2 <= D <= nx                         */
+  int64_t nx;            /* marched columns, >= D                                */
+  int64_t nt;            /* rows, >= 1                                           */
+  double delta;          /* grid step > 0                                        */
+  double gamma;          /* decay rate Gamma > 0                                 */
+  double omega0;         /* two-level-system frequency w0                        */
+  double k;              /* incident carrier wavenumber                          */
+  int32_t init_cond;     /* fdtd_init_cond                                       */
+  int32_t precision;     /* fdtd_precision                                       */
+  double alpha;          /* exponential width in units of Gamma (> 0; IC 2, 3)   */
+  double sigma;          /* Gaussian width (> 0; IC 4)                           */
+  double center;         /* Gaussian centre x_c (IC 4); the pulse is cut at x=-a */
+  int32_t tstep;         /* keep every (tstep+1)-th row as a snapshot; -1: none  */
+  int32_t rows_per_launch; /* rows marched per kernel launch; 0 = default        */
+} fdtd_params;
+
+/* fdtd_set_boundary sources */
+enum {
+  FDTD_BOUNDARY_ANALYTIC = 0, /* e(t) by the library's gamma(n,z) / quadrature kernel */
+  FDTD_BOUNDARY_TABLE = 1     /* e(r delta), r = 0..nt-1, complex128, given on device */
+};
+
+/* fdtd_readout kinds */
+enum {
+  FDTD_READ_ROW = 0,       /* last marched row: nx complex (precision's type)       */
+  FDTD_READ_NORMS = 1,     /* N(n) for n = 0..rows_done-1: FP64                     */
+  FDTD_READ_SNAPSHOTS = 2, /* rows 0, tstep+1, 2(tstep+1), ... marched so far       */
+  FDTD_READ_ETABLE = 3,    /* e(r delta), r = 0..nt-1: complex128                   */
+  FDTD_READ_ROWS_DONE = 4  /* int64: rows available (row 0 counts)                  */
+};
+
+/*
+ * fdtd_plan -- validate parameters and size the workspace.
+ *   p            : array of n_instances parameter sets (host memory, read only;
+ *                  copied).  This build supports n_instances == 1.
+ *   cuda_stream  : cudaStream_t the plan queues its work on (NULL = default).
+ *   workspace_bytes (out): device bytes the caller must lend (256-byte aligned).
+ *   out (out)    : new plan handle, released by fdtd_destroy.
+ * Derivation (Sec. 2, Eq. 3a-c, App. A): a = D delta / 2, W = i w0 + Gamma/2,
+ * A = 1/delta + W/4; the update coefficients are (1/delta - W/4)/A, -(W/4)/A,
+ * (Gamma/8)/A and 1/A.  Errors: FDTD_ERR_INVALID_ARG (D odd, D > nx, delta <= 0,
+ * ...), FDTD_ERR_UNSUPPORTED, FDTD_ERR_CUDA.
+ */
+fdtd_status fdtd_plan(const fdtd_params* p, int32_t n_instances, void* cuda_stream, size_t* workspace_bytes,
+                      fdtd_plan_t* out);
+
+/* fdtd_bind_workspace -- lend `bytes` of device memory at `device_ptr`
+ * (256-byte aligned, >= the size fdtd_plan reported) for the plan's lifetime.
+ * Errors: FDTD_ERR_WORKSPACE, FDTD_ERR_STATE. */
+fdtd_status fdtd_bind_workspace(fdtd_plan_t plan, void* device_ptr, size_t bytes);
+
+/*
+ * fdtd_set_boundary -- build the boundary and reset the march to row 0.
+ * Computes e(t) on the rows (Sec. 2 (b) e1 series; Sec. 2 (c) e0 series with
+ * gamma(n+1,-ip(t-2na)) from App. C; quadrature for Gaussian photons), the
+ * wavepacket table phi(-a - j delta), the per-row source scalars, and zeroes
+ * the ring.  source = FDTD_BOUNDARY_TABLE takes e(r delta) from device_table
+ * (n = nt complex128 values, device memory, read during the call's kernels)
+ * instead of computing it.  Asynchronous.  Errors: FDTD_ERR_STATE (no
+ * workspace), FDTD_ERR_INVALID_ARG, FDTD_ERR_CUDA.
+ */
+fdtd_status fdtd_set_boundary(fdtd_plan_t plan, int32_t source, const void* device_table, int64_t n);
+
+/*
+ * fdtd_march -- march n_rows more rows (clamped to nt), asynchronously on the
+ * plan's stream.  Each row n solves Eq. 1's discretisation at every marched
+ * column; the delay term reads rows n-D and n-D-1 from the ring.  Errors:
+ * FDTD_ERR_STATE (no boundary), FDTD_ERR_INVALID_ARG (n_rows < 0),
+ * FDTD_ERR_CUDA.
+ */
+fdtd_status fdtd_march(fdtd_plan_t plan, int64_t n_rows);
+
+/*
+ * fdtd_readout -- synchronise the plan's stream and copy `kind` into dst.
+ *   dst       : caller-owned host or device memory (cudaMemcpyDefault).
+ *   dst_bytes : capacity of dst; FDTD_ERR_INVALID_ARG if too small.
+ * Returns a latched device error (FDTD_ERR_TIMEOUT / FDTD_ERR_BOUNDS) first.
+ * Norms: N(n) = delta * trapezoid of |psi(x, n delta)|^2 over x = -a (exact
+ * boundary value) .. the last marched column, accumulated in FP64 (App. D).
+ */
+fdtd_status fdtd_readout(fdtd_plan_t plan, int32_t kind, void* dst, int64_t dst_bytes);
+
+/* Size in bytes that fdtd_readout(kind) writes at the current state. */
+int64_t fdtd_readout_bytes(fdtd_plan_t plan, int32_t kind);
+
+/* fdtd_destroy -- release the host-side plan (not the workspace). NULL is a no-op. */
+void fdtd_destroy(fdtd_plan_t plan);
+
+/* Static description of a status code. */
+const char* fdtd_status_string(fdtd_status s);
+
+/* Last error message recorded on the plan (empty string if none). */
+const char* fdtd_last_error(fdtd_plan_t plan);
+
+/*
+ * fdtd_gamma_star -- the App. C routine on its own: for i < count,
+ *   out[i] = Gamma(n[i]) * gamma*(n[i], z[i]) = int_0^1 s^(n-1) e^(-z s) ds,
+ * so gamma(n,z) = z^n out and P(n,z) = z^n out / (n-1)!.  n[i] >= 1 (int32),
+ * z and out are interleaved complex128.  All three pointers are device memory;
+ * the kernel runs on cuda_stream and the call returns without synchronising.
+ * Errors: FDTD_ERR_INVALID_ARG (count < 0 or a NULL pointer), FDTD_ERR_CUDA.
+ */
+fdtd_status fdtd_gamma_star(const int32_t* n, const double* z, double* out, int64_t count, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDTD_H_ */

@@ -1,0 +1,101 @@
+"""Synthetic workloads shaped like the paper's runs, and their seeded draws.
+
+Pure data: sizes and physical parameters of each workload, plus a SplitMix64
+generator for the seeded parameter sets.  Nothing here computes any part of
+the method; both the CUDA path and the CPU oracle take their inputs from
+this module.
+
+Units follow the paper's figure captions (c = 1): a is the atom-mirror
+distance, D = 2a/delta grid steps, k0 a the phase, and the incident carrier
+is resonant, k = w0 = k0 (Figs. 5, 6-left, 9 use k = w0).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, replace
+
+PI = math.pi
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    nx: int            # marched columns in x > -a
+    nt: int            # rows
+    D: int             # 2a / delta
+    delta: float
+    gamma: float
+    omega0: float
+    k: float
+    init_cond: int     # 2 stimulated emission, 3 two exponential photons, 4 two Gaussian photons
+    alpha: float = 1.0
+    sigma: float = 0.0
+    center: float = 0.0
+
+    @property
+    def a(self) -> float:
+        return 0.5 * self.D * self.delta
+
+    @property
+    def updates(self) -> int:
+        """Grid-point updates of one full march (rows 1..nt-1, every marched column)."""
+        return self.nx * (self.nt - 1)
+
+    def with_(self, **kw) -> "Workload":
+        return replace(self, **kw)
+
+
+def exp_pair(nx, nt, D=40, a=1.0, gamma=1.0, k0a=PI / 2, alpha=1.0, name="exp") -> Workload:
+    """Two identical exponential photons of width 1/(alpha Gamma) (Sec. 2 (c))."""
+    w0 = k0a / a
+    return Workload(name, nx, nt, D, 2 * a / D, gamma, w0, w0, 3, alpha=alpha)
+
+
+def gauss_pair(nx, nt, D, a, gamma, k0a, sigma, lead=8.0, name="gauss") -> Workload:
+    """Two identical Gaussian photons, centred `lead` sigma left of x = -a."""
+    w0 = k0a / a
+    return Workload(name, nx, nt, D, 2 * a / D, gamma, w0, w0, 4, sigma=sigma, center=-a - lead * sigma)
+
+
+# The workloads.  "small": Gamma = 1, 2a = 2 (D = 40 at delta = 0.05), k0 a = pi/2,
+# exponential two-photon packet of width 1/Gamma, 1024 x 4096 (complex128).
+SMALL = exp_pair(1024, 4096, name="exp_pair_D40_nx1024_nt4096")
+# "large": one FP64 instance, 2^20 x 2^18, D = 2000 (2a = 20/Gamma), k0 a = 0.3 pi,
+# Gaussian pulse sigma = 5/Gamma, ring of D+2 rows x 2^20 complex128 in HBM.
+LARGE = gauss_pair(1 << 20, 1 << 18, D=2000, a=10.0, gamma=1.0, k0a=0.3 * PI, sigma=5.0,
+                   name="gauss_pair_D2000_nx1M_nt256k")
+# "precision": the small physics at 8192 x 32768, marched in complex64.
+PRECISION = exp_pair(8192, 32768, name="exp_pair_D40_nx8192_nt32768")
+
+
+# ---- seeded draws -----------------------------------------------------------
+
+class SplitMix64:
+    """SplitMix64 (Steele, Lea, Flood 2014): 64-bit state, golden-ratio increment."""
+
+    MASK = (1 << 64) - 1
+
+    def __init__(self, seed: int):
+        self.s = seed & self.MASK
+
+    def next_u64(self) -> int:
+        self.s = (self.s + 0x9E3779B97F4A7C15) & self.MASK
+        z = self.s
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & self.MASK
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & self.MASK
+        return z ^ (z >> 31)
+
+    def uniform(self, lo=0.0, hi=1.0) -> float:
+        return lo + (hi - lo) * ((self.next_u64() >> 11) * (1.0 / (1 << 53)))
+
+
+def jittered(base: Workload, seed: int, n: int) -> list[Workload]:
+    """Parity cases around `base`: detuning k - w0 ~ U[-Gamma, Gamma] and
+    alpha ~ U[0.5, 2] (p = k - w0 + i Gamma (1-alpha)/2 away from 0)."""
+    g = SplitMix64(seed)
+    out = []
+    for i in range(n):
+        dk = g.uniform(-base.gamma, base.gamma)
+        al = g.uniform(0.5, 2.0)
+        out.append(base.with_(k=base.omega0 + dk, alpha=al, name=f"{base.name}_jit{i}"))
+    return out
