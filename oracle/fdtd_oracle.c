@@ -327,7 +327,9 @@ static void gl_init(void) {
  *   F_j(u) = int_0^u (u-v)^j e^{-W(u-v)} / j!  g(v) dv,  g(v) = sqrt(Gamma/2) phi(-a-v).
  * Each F_j is integrated by composite Gauss-Legendre on the part of [0,u]
  * where the Gaussian exceeds e^-40 of its peak; the panel count is doubled
- * until two successive values agree to 1e-15 of the integral of |integrand|. */
+ * until two successive values agree to 4e-14 of the integral of |integrand|
+ * (each node carries ~|log-space exponent| x 1e-16 ~ 5e-15 of rounding, so
+ * tighter agreement is noise), or to 1e-20 absolute (|e(t)| <= 1). */
 static cplx gauss_F(const orc_params* p, int j, double u, int panels, double* l1) {
   double a = half_a(p), s2 = p->sigma * p->sigma;
   double s0 = -a - p->center; /* g peaks at v = s0 */
@@ -371,7 +373,7 @@ static int gauss_h(const orc_params* p, double tau, cplx* out) {
     for (int it = 0; it < 8; ++it) {
       panels *= 2;
       cur = gauss_F(p, j, u, panels, &l1);
-      if (cabs(cur - prev) <= 1e-15 * (cabs(cur) + l1) || l1 == 0.0) break;
+      if (cabs(cur - prev) <= 4e-14 * (cabs(cur) + l1) || cabs(cur - prev) <= 1e-20) break;
       if (it == 7) st = ORC_NOT_CONVERGED;
       prev = cur;
     }

@@ -57,13 +57,21 @@ def check_parity(F, oracle, w, **kw):
     g = run_gpu(F, w, **kw)
     r = oracle.march(oparams(oracle, w), tstep=0, want_etab=True)
     assert g["rows"] == w.nt
-    e_err = np.max(np.abs(g["etab"] - r["etab"])) / np.max(np.abs(r["etab"]))
+    e_err = np.max(np.abs(g["etab"] - r["etab"])) / max(np.max(np.abs(r["etab"])), 1e-300)
     assert e_err < 1e-13, e_err
+    if not np.any(r["snaps"]):  # nothing marched yet (nt = 1): exact zeros
+        assert not np.any(g["snaps"])
+        return 0.0
     err = rel_l2(g["snaps"], r["snaps"])
     assert err < 1e-12, err
-    big = r["norms"] > 1e-12 * r["norms"].max()
-    nerr = np.max(np.abs(g["norms"][big] - r["norms"][big]) / r["norms"][big])
+    # norms: a row's absolute error is set by the largest amplitudes of the march,
+    # so it is measured against the largest norm; rows within 1e-6 of it also
+    # agree to 1e-9 relative
+    nmax = r["norms"].max()
+    nerr = np.max(np.abs(g["norms"] - r["norms"])) / nmax
     assert nerr < 1e-12, nerr
+    big = r["norms"] > 1e-6 * nmax
+    assert np.max(np.abs(g["norms"][big] - r["norms"][big]) / r["norms"][big]) < 1e-9
     assert np.array_equal(g["last"], g["snaps"][-1])
     return err
 
