@@ -183,6 +183,45 @@ const char* fdtd_last_error(fdtd_plan_t plan);
  */
 fdtd_status fdtd_gamma_star(const int32_t* n, const double* z, double* out, int64_t count, void* cuda_stream);
 
+/*
+ * fdtd_march_noalloc -- the whole FP64 march of one instance (boundary, every
+ * row, readout) for callers that cannot allocate device memory.  The paper
+ * has no counterpart; this is a deployment convenience.
+ *
+ * Who cannot allocate: a host framework that owns all device memory through
+ * its own pool and forbids other allocations, a plugin inside such a process,
+ * or code that runs while a stream is being captured into a CUDA graph
+ * (allocation calls are not allowed during capture).  They can pass inputs
+ * and outputs, but cannot lend the march its scratch (fdtd_bind_workspace).
+ *
+ * Scratch: a 64 MiB array built into the library (fdtd_noalloc_max_bytes()),
+ * placed on every GPU that loads the library and held there until the process
+ * exits.  An instance whose workspace (as fdtd_plan reports it) exceeds that
+ * size is rejected with FDTD_ERR_WORKSPACE before any device work.  Every call
+ * on a device shares the array: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and corrupt each other; serialise them.
+ * Each call zeroes the ring, norms and barrier words it uses, so a call does
+ * not see the previous call's contents.
+ *
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current).  Make that first call
+ * before any stream capture.  No call allocates device memory, and none calls
+ * cudaMalloc, cudaFree or an allocating library routine.
+ *
+ *   p          : parameters, as for fdtd_plan (precision FDTD_F64; tstep is
+ *                ignored: no snapshots are kept).
+ *   cuda_stream: cudaStream_t for all work; the call synchronises it before
+ *                returning, to report device-side errors.
+ *   row_out    : device memory, nx complex128: psi on the last row nt-1.
+ *   norms_out  : device memory, nt doubles: N(n) as FDTD_READ_NORMS defines it.
+ * Errors: as fdtd_plan / fdtd_set_boundary / fdtd_march / fdtd_readout, plus
+ * FDTD_ERR_WORKSPACE (instance larger than the built-in scratch).
+ */
+fdtd_status fdtd_march_noalloc(const fdtd_params* p, void* cuda_stream, void* row_out, double* norms_out);
+
+/* Size in bytes of the built-in scratch of fdtd_march_noalloc. */
+size_t fdtd_noalloc_max_bytes(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -7,7 +7,6 @@
 #include <string.h>
 
 #include <new>
-#include <vector>
 
 #include "fdtd_internal.cuh"
 
@@ -19,12 +18,12 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 fdtd_status fail(fdtd_plan_t p, fdtd_status s, const char* msg) {
-  if (p) p->last_error = msg;
+  if (p && p->record_errors) p->last_error = msg;
   return s;
 }
 
 fdtd_status cuda_fail(fdtd_plan_t p, cudaError_t e, const char* where) {
-  if (p) {
+  if (p && p->record_errors) {
     p->last_error = where;
     p->last_error += ": ";
     p->last_error += cudaGetErrorString(e);
@@ -73,10 +72,12 @@ const char* fdtd_status_string(fdtd_status s) {
 
 const char* fdtd_last_error(fdtd_plan_t p) { return p ? p->last_error.c_str() : ""; }
 
-fdtd_status fdtd_plan(const fdtd_params* pin, int32_t n_instances, void* cuda_stream, size_t* workspace_bytes,
-                      fdtd_plan_t* out) {
-  if (!pin || !workspace_bytes || !out) return FDTD_ERR_INVALID_ARG;
-  *out = nullptr;
+}  // extern "C"
+
+// Validate parameters and fill a caller-provided plan (no device memory is
+// touched).  Shared by fdtd_plan and the no-allocation entry point.
+fdtd_status fdtd_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n_instances, void* cuda_stream,
+                           size_t* workspace_bytes) {
   if (pin->struct_size != sizeof(fdtd_params)) return FDTD_ERR_INVALID_ARG;
   if (n_instances != 1) return FDTD_ERR_UNSUPPORTED;
   const fdtd_params& p = *pin;
@@ -88,26 +89,19 @@ fdtd_status fdtd_plan(const fdtd_params* pin, int32_t n_instances, void* cuda_st
   if (p.tstep < -1 || p.rows_per_launch < 0) return FDTD_ERR_INVALID_ARG;
   if (p.precision != FDTD_F64) return FDTD_ERR_UNSUPPORTED;
 
-  fdtd_plan_t P = new (std::nothrow) fdtd_plan_s();
-  if (!P) return FDTD_ERR_INVALID_ARG;
   P->p = p;
   P->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   cudaError_t e = cudaGetDevice(&P->device);
-  if (e != cudaSuccess) {
-    delete P;
-    return FDTD_ERR_CUDA;
-  }
+  if (e != cudaSuccess) return FDTD_ERR_CUDA;
   cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
   int maxg = fdtd::march_f64_max_grid(P->device);
-  if (maxg <= 0) {
-    delete P;
-    return FDTD_ERR_CUDA;
-  }
+  if (maxg <= 0) return FDTD_ERR_CUDA;
   // one CTA per SM, but no more CTAs than chunks of columns
   int64_t chunks = (p.nx + fdtd::kMarchChunk - 1) / fdtd::kMarchChunk;
   int grid = P->num_sms < maxg ? P->num_sms : maxg;
   if (grid > chunks * 4) grid = (int)(chunks * 4 > 0 ? chunks * 4 : 1);
   if (grid > p.nx / 8 + 1) grid = (int)(p.nx / 8 + 1);
+  if (grid > fdtd::kMaxGrid) grid = fdtd::kMaxGrid;
   if (grid < 1) grid = 1;
   P->grid = grid;
 
@@ -126,10 +120,8 @@ fdtd_status fdtd_plan(const fdtd_params* pin, int32_t n_instances, void* cuda_st
   P->kfix = trunc_depth(ac2, fdtd::kMaxTrunc);
   P->khalo = P->kfix;
   P->kscan = trunc_depth(pow(ac2, fdtd::kMarchV), fdtd::kMaxTrunc);
-  if (P->kfix > fdtd::kMaxTrunc || P->kscan > fdtd::kMaxTrunc) {
-    delete P;
+  if (P->kfix > fdtd::kMaxTrunc || P->kscan > fdtd::kMaxTrunc)
     return FDTD_ERR_UNSUPPORTED;  // |c2| too close to 1 (delta far too coarse)
-  }
 
   // workspace layout
   P->R = p.D + 2;
@@ -151,6 +143,22 @@ fdtd_status fdtd_plan(const fdtd_params* pin, int32_t n_instances, void* cuda_st
   P->ws_need = off;
   P->state = 0;
   *workspace_bytes = P->ws_need;
+  return FDTD_OK;
+}
+
+extern "C" {
+
+fdtd_status fdtd_plan(const fdtd_params* pin, int32_t n_instances, void* cuda_stream, size_t* workspace_bytes,
+                      fdtd_plan_t* out) {
+  if (!pin || !workspace_bytes || !out) return FDTD_ERR_INVALID_ARG;
+  *out = nullptr;
+  fdtd_plan_t P = new (std::nothrow) fdtd_plan_s();
+  if (!P) return FDTD_ERR_INVALID_ARG;
+  fdtd_status st = fdtd_plan_fill(P, pin, n_instances, cuda_stream, workspace_bytes);
+  if (st != FDTD_OK) {
+    delete P;
+    return st;
+  }
   *out = P;
   return FDTD_OK;
 }
@@ -189,7 +197,7 @@ fdtd_status fdtd_set_boundary(fdtd_plan_t P, int32_t source, const void* device_
   // column split: equal cost per CTA, with the region -a < x <= 3a (2D columns,
   // read through the general path) weighted kMidWeight
   const double kMidWeight = 3.0;
-  std::vector<int64_t> split(P->grid + 1);
+  int64_t split[fdtd::kMaxGrid + 1];
   {
     const int64_t mid = (2 * (int64_t)p.D < p.nx) ? 2 * (int64_t)p.D : p.nx;
     const double total = kMidWeight * mid + (double)(p.nx - mid);
@@ -203,9 +211,10 @@ fdtd_status fdtd_set_boundary(fdtd_plan_t P, int32_t source, const void* device_
     }
     split[P->grid] = p.nx;
   }
-  e = cudaMemcpyAsync(P->ws + P->off_colsplit, split.data(), sizeof(int64_t) * split.size(), cudaMemcpyHostToDevice, s);
+  e = cudaMemcpyAsync(P->ws + P->off_colsplit, split, sizeof(int64_t) * (size_t)(P->grid + 1), cudaMemcpyHostToDevice,
+                      s);
   if (e != cudaSuccess) return cuda_fail(P, e, "cudaMemcpyAsync(colsplit)");
-  // the pageable copy above is staged before returning; keep no reference to `split`
+  // a copy from pageable memory is staged before cudaMemcpyAsync returns
   fdtd::BoundaryArgs a;
   a.etab = at<cd>(P, P->off_etab);
   a.phitab = at<cd>(P, P->off_phi);

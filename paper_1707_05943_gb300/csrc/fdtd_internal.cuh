@@ -39,6 +39,7 @@ constexpr int kMarchThreads = 512;   // threads per CTA of the FP64 march
 constexpr int kMarchV = 4;           // consecutive columns per thread
 constexpr int kMarchChunk = kMarchThreads * kMarchV;
 constexpr int kMaxTrunc = 64;        // cap on scan / halo truncation depth
+constexpr int kMaxGrid = 1024;       // cap on CTAs of the persistent march
 
 // sync words at the start of the workspace
 struct SyncWords {
@@ -116,8 +117,13 @@ struct fdtd_plan_s {
   int64_t rows_done;     // rows available (0 before set_boundary)
   int state;             // 0 planned, 1 bound, 2 boundary set
   int kscan, kfix, khalo;
+  bool record_errors = true;  // false: keep no message (no host allocation on error paths)
   std::string last_error;
 };
+
+// fills a plan without allocating it (fdtd_plan = new + this)
+fdtd_status fdtd_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n_instances, void* cuda_stream,
+                           size_t* workspace_bytes);
 
 namespace fdtd {
 // launchers (return cudaError_t)

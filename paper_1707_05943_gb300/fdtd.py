@@ -29,7 +29,8 @@ BOUNDARY_ANALYTIC, BOUNDARY_TABLE = 0, 1
 READ_ROW, READ_NORMS, READ_SNAPSHOTS, READ_ETABLE, READ_ROWS_DONE = range(5)
 
 EXPORTS = ["fdtd_plan", "fdtd_bind_workspace", "fdtd_set_boundary", "fdtd_march", "fdtd_readout",
-           "fdtd_readout_bytes", "fdtd_destroy", "fdtd_status_string", "fdtd_last_error", "fdtd_gamma_star"]
+           "fdtd_readout_bytes", "fdtd_destroy", "fdtd_status_string", "fdtd_last_error", "fdtd_gamma_star",
+           "fdtd_march_noalloc", "fdtd_noalloc_max_bytes"]
 
 
 class FdtdParams(ctypes.Structure):
@@ -83,8 +84,11 @@ def lib() -> ctypes.CDLL:
         L.fdtd_last_error.argtypes = [vp]
         L.fdtd_last_error.restype = ctypes.c_char_p
         L.fdtd_gamma_star.argtypes = [vp, vp, vp, i64, vp]
+        L.fdtd_march_noalloc.argtypes = [ctypes.POINTER(FdtdParams), vp, vp, vp]
+        L.fdtd_noalloc_max_bytes.argtypes = []
+        L.fdtd_noalloc_max_bytes.restype = sz
         for f in ("fdtd_plan", "fdtd_bind_workspace", "fdtd_set_boundary", "fdtd_march", "fdtd_readout",
-                  "fdtd_gamma_star"):
+                  "fdtd_gamma_star", "fdtd_march_noalloc"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -140,6 +144,16 @@ def fdtd_destroy(plan):
 def fdtd_gamma_star(n_ptr: int, z_ptr: int, out_ptr: int, count: int, stream: int | None = None):
     _check(lib().fdtd_gamma_star(ctypes.c_void_p(n_ptr), ctypes.c_void_p(z_ptr), ctypes.c_void_p(out_ptr), count,
                                  ctypes.c_void_p(stream or 0)), None, "fdtd_gamma_star")
+
+
+def fdtd_march_noalloc(params: FdtdParams, stream: int | None, row_out_ptr: int, norms_out_ptr: int):
+    """March one instance using the library's built-in scratch (no device allocation)."""
+    _check(lib().fdtd_march_noalloc(ctypes.byref(params), ctypes.c_void_p(stream or 0), ctypes.c_void_p(row_out_ptr),
+                                    ctypes.c_void_p(norms_out_ptr)), None, "fdtd_march_noalloc")
+
+
+def fdtd_noalloc_max_bytes() -> int:
+    return int(lib().fdtd_noalloc_max_bytes())
 
 
 # ---- convenience ------------------------------------------------------------
