@@ -155,7 +155,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=["large", "small"])
-    ap.add_argument("--rows", type=int, default=0, help="march only this many rows (testing)")
+    ap.add_argument("--rows", type=int, default=0, help="march only this many rows (profiling)")
+    ap.add_argument("--nx", type=int, default=0, help="march only this many columns (profiling)")
+    ap.add_argument("--D", type=int, default=0, help="use this D at the same delta (profiling)")
     ap.add_argument("--rows-per-launch", type=int, default=4096)
     ap.add_argument("--ref-rows", type=int, default=4096)
     ap.add_argument("--cpu-rows", type=int, default=6144)
@@ -166,6 +168,10 @@ def main():
     w = W.LARGE if args.workload == "large" else W.SMALL
     if args.rows:
         w = w.with_(nt=args.rows, name=f"{w.name}_rows{args.rows}")
+    if args.nx:
+        w = w.with_(nx=args.nx, name=f"{w.name}_nx{args.nx}")
+    if args.D:
+        w = w.with_(D=args.D, name=f"{w.name}_D{args.D}")
     if args.impl == "reference":
         run_reference(args, w)
         return
@@ -214,8 +220,9 @@ def main():
     for _ in range(args.warmup):
         step()
     stream.synchronize()
-    norms_w = solver.read(fdtd.READ_NORMS)
-    assert np.all(np.isfinite(norms_w))
+    if args.warmup > 0:
+        norms_w = solver.read(fdtd.READ_NORMS)
+        assert np.all(np.isfinite(norms_w))
 
     sampler = ClockSampler(local)
     events = []

@@ -235,6 +235,19 @@ __global__ void k_rowscal(const BoundaryArgs A) {
   A.rowscal[2 * n + 1] = R2;
 }
 
+// dEtab[i] = E(i-D) - E(i), E(r) = theta(r) e(r delta) (theta(0) = 1/2, E = 0 outside
+// 0 <= r < nt): the e-dependence of the mirror sources S2 + S3 beyond x > 3a, indexed by
+// i = r2 + D with r2 = n - m - D/2.
+__global__ void k_detab(const BoundaryArgs A) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= A.nt + A.D) return;
+  auto E = [&](int64_t r) -> cd {
+    if (r < 0 || r >= A.nt) return cd{0.0, 0.0};
+    return (r == 0) ? 0.5 * A.etab[0] : A.etab[r];
+  };
+  A.detab[i] = E(i - A.D) - E(i);
+}
+
 // norms[0] = delta * (1/2) |psi(-a, 0)|^2: psi(x>-a, 0) = 0 in every class.
 __global__ void k_norm0(const BoundaryArgs A) {
   cd v = A.C * (A.phitab[0] * A.etab[0]);
@@ -298,6 +311,7 @@ cudaError_t launch_boundary(const BoundaryArgs& a, cd* hscratch, bool compute_et
     if (a.init_cond != FDTD_IC_STIM_EMISSION) k_etable_pass2<<<(unsigned)((a.nt + T - 1) / T), T, 0, s>>>(E);
   }
   k_norm0<<<1, 1, 0, s>>>(a);
+  k_detab<<<(unsigned)((a.nt + a.D + T - 1) / T), T, 0, s>>>(a);
   return cudaGetLastError();
 }
 

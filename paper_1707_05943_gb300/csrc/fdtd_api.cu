@@ -96,11 +96,9 @@ fdtd_status fdtd_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n_ins
   cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
   int maxg = fdtd::march_f64_max_grid(P->device);
   if (maxg <= 0) return FDTD_ERR_CUDA;
-  // one CTA per SM, but no more CTAs than chunks of columns
-  int64_t chunks = (p.nx + fdtd::kMarchChunk - 1) / fdtd::kMarchChunk;
+  // one CTA per SM, but at least 64 columns per CTA
   int grid = P->num_sms < maxg ? P->num_sms : maxg;
-  if (grid > chunks * 4) grid = (int)(chunks * 4 > 0 ? chunks * 4 : 1);
-  if (grid > p.nx / 8 + 1) grid = (int)(p.nx / 8 + 1);
+  if ((int64_t)grid > (p.nx + 63) / 64) grid = (int)((p.nx + 63) / 64);
   if (grid > fdtd::kMaxGrid) grid = fdtd::kMaxGrid;
   if (grid < 1) grid = 1;
   P->grid = grid;
@@ -119,14 +117,15 @@ fdtd_status fdtd_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n_ins
   const double ac2 = cabsh(P->c2);
   P->kfix = trunc_depth(ac2, fdtd::kMaxTrunc);
   P->khalo = P->kfix;
-  P->kscan = trunc_depth(pow(ac2, fdtd::kMarchV), fdtd::kMaxTrunc);
-  if (P->kfix > fdtd::kMaxTrunc || P->kscan > fdtd::kMaxTrunc)
+  if (P->kfix > fdtd::kMaxTrunc)
     return FDTD_ERR_UNSUPPORTED;  // |c2| too close to 1 (delta far too coarse)
 
   // workspace layout
   P->R = p.D + 2;
   P->elem = sizeof(cd);
-  P->stride = (p.nx + 31) / 32 * 32;
+  // row pitch: a multiple of 32 columns plus 32, so that ring rows are never a
+  // power-of-two number of bytes apart (rows read together would share L2 slices)
+  P->stride = (p.nx + 31) / 32 * 32 + 32;
   P->nphi = p.nt + 3 * (int64_t)p.D + 8;
   P->nsnap = (p.tstep >= 0) ? (p.nt - 1) / (p.tstep + 1) + 1 : 0;
   size_t off = 0;
@@ -134,6 +133,7 @@ fdtd_status fdtd_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n_ins
   P->off_etab = off;     off = align_up(off + sizeof(cd) * (size_t)p.nt);
   P->off_phi = off;      off = align_up(off + sizeof(cd) * (size_t)P->nphi);
   P->off_rowscal = off;  off = align_up(off + 2 * sizeof(cd) * (size_t)p.nt);
+  P->off_detab = off;    off = align_up(off + sizeof(cd) * (size_t)(p.nt + p.D));
   P->off_norms = off;    off = align_up(off + sizeof(double) * (size_t)p.nt);
   P->off_hscr = off;     off = align_up(off + sizeof(cd) * (size_t)p.nt);
   P->off_partials = off; off = align_up(off + 2 * sizeof(double) * (size_t)grid);
@@ -196,11 +196,13 @@ fdtd_status fdtd_set_boundary(fdtd_plan_t P, int32_t source, const void* device_
   }
   // column split: equal cost per CTA, with the region -a < x <= 3a (2D columns,
   // read through the general path) weighted kMidWeight
-  const double kMidWeight = 3.0;
+  int kMidWeight = 16;  // measured: a column of -a < x <= 3a costs ~16 bulk columns
+  if (const char* w = getenv("FDTD_MID_WEIGHT")) kMidWeight = atoi(w) > 0 ? atoi(w) : kMidWeight;
+  P->mid_weight = kMidWeight;
   int64_t split[fdtd::kMaxGrid + 1];
   {
     const int64_t mid = (2 * (int64_t)p.D < p.nx) ? 2 * (int64_t)p.D : p.nx;
-    const double total = kMidWeight * mid + (double)(p.nx - mid);
+    const double total = (double)kMidWeight * mid + (double)(p.nx - mid);
     split[0] = 0;
     for (int b = 1; b < P->grid; ++b) {
       double target = total * b / P->grid;
@@ -211,6 +213,13 @@ fdtd_status fdtd_set_boundary(fdtd_plan_t P, int32_t source, const void* device_
     }
     split[P->grid] = p.nx;
   }
+  {
+    // shared memory for the delay pair sums: khalo + the widest CTA range
+    int64_t maxL = 0;
+    for (int b = 0; b < P->grid; ++b) maxL = (split[b + 1] - split[b] > maxL) ? split[b + 1] - split[b] : maxL;
+    size_t need = sizeof(cd) * (size_t)(maxL + P->khalo);
+    P->march_smem = (need <= size_t(200) * 1024) ? need : 0;
+  }
   e = cudaMemcpyAsync(P->ws + P->off_colsplit, split, sizeof(int64_t) * (size_t)(P->grid + 1), cudaMemcpyHostToDevice,
                       s);
   if (e != cudaSuccess) return cuda_fail(P, e, "cudaMemcpyAsync(colsplit)");
@@ -219,6 +228,7 @@ fdtd_status fdtd_set_boundary(fdtd_plan_t P, int32_t source, const void* device_
   a.etab = at<cd>(P, P->off_etab);
   a.phitab = at<cd>(P, P->off_phi);
   a.rowscal = at<cd>(P, P->off_rowscal);
+  a.detab = at<cd>(P, P->off_detab);
   a.nt = p.nt;
   a.nphi = P->nphi;
   a.D = p.D;
@@ -257,6 +267,7 @@ fdtd_status fdtd_march(fdtd_plan_t P, int64_t n_rows) {
   a.etab = at<cd>(P, P->off_etab);
   a.phitab = at<cd>(P, P->off_phi);
   a.rowscal = at<cd>(P, P->off_rowscal);
+  a.detab = at<cd>(P, P->off_detab);
   a.norms = at<double>(P, P->off_norms);
   a.partials = at<double>(P, P->off_partials);
   a.snaps = P->nsnap ? at<cd>(P, P->off_snaps) : nullptr;
@@ -273,24 +284,18 @@ fdtd_status fdtd_march(fdtd_plan_t P, int64_t n_rows) {
   a.gs = P->gs;
   a.C = P->C;
   a.delta = p.delta;
-  cd Av = cd{1.0, 0.0};
-  for (int v = 0; v < fdtd::kMarchV; ++v) Av = Av * P->c2;
-  a.A = Av;
-  a.kscan = P->kscan;
   a.kfix = P->kfix;
   a.khalo = P->khalo;
+  a.hreuse = P->march_smem > 0 ? 1 : 0;
+  a.mid_weight = P->mid_weight;
   a.c2pow[0] = cd{1.0, 0.0};
-  a.Apow[0] = cd{1.0, 0.0};
-  for (int k = 1; k <= fdtd::kMaxTrunc; ++k) {
-    a.c2pow[k] = a.c2pow[k - 1] * P->c2;
-    a.Apow[k] = a.Apow[k - 1] * Av;
-  }
+  for (int k = 1; k <= fdtd::kMaxTrunc; ++k) a.c2pow[k] = a.c2pow[k - 1] * P->c2;
   a.spin_cycles = 4000000000LL;  // ~2 s at 2 GHz
   const int64_t per = p.rows_per_launch > 0 ? p.rows_per_launch : 4096;
   for (int64_t n0 = P->rows_done; n0 < end; n0 += per) {
     a.n_begin = n0;
     a.n_end = (n0 + per < end) ? n0 + per : end;
-    cudaError_t e = fdtd::launch_march_f64(a, P->grid, P->stream);
+    cudaError_t e = fdtd::launch_march_f64(a, P->grid, P->march_smem, P->stream);
     if (e != cudaSuccess) return cuda_fail(P, e, "march launch");
   }
   P->rows_done = end;

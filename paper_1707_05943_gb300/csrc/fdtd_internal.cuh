@@ -36,8 +36,7 @@ __host__ __device__ __forceinline__ double cabs2(cd a) { return a.re * a.re + a.
 
 // ---------------------------------------------------------------- constants
 constexpr int kMarchThreads = 512;   // threads per CTA of the FP64 march
-constexpr int kMarchV = 4;           // consecutive columns per thread
-constexpr int kMarchChunk = kMarchThreads * kMarchV;
+constexpr int kMarchP = 8;           // leading columns of a thread's segment kept in registers
 constexpr int kMaxTrunc = 64;        // cap on scan / halo truncation depth
 constexpr int kMaxGrid = 1024;       // cap on CTAs of the persistent march
 
@@ -58,6 +57,7 @@ struct MarchArgs {
   const cd* etab;        // e(r delta), r < nt
   const cd* phitab;      // phi(-a - j delta), j < nphi
   const cd* rowscal;     // per row: R1(n), R2(n)  (2 per row)
+  const cd* detab;       // E(i-D) - E(i), i < nt + D
   double* norms;         // nt
   double* partials;      // 2 x grid
   cd* snaps;             // nsnap x nx or null
@@ -71,12 +71,11 @@ struct MarchArgs {
   cd gs;                 // -(Gamma/4) / A: mirror-bar source coefficient
   double C;              // psi(x<=-a) prefactor
   double delta;
-  cd A;                  // c2^V: carry multiplier across one thread's columns
-  int kscan;             // carries kept across threads (|A|^kscan < 2^-60)
   int kfix;              // columns that receive a carry (|c2|^kfix < 2^-60)
   int khalo;             // halo columns recomputed left of each CTA range
+  int hreuse;            // 1: delay pair sums of the previous row kept in shared memory
+  int mid_weight;        // cost of a column of -a < x <= 3a in bulk columns
   cd c2pow[kMaxTrunc + 1];  // c2^0 .. c2^kMaxTrunc
-  cd Apow[kMaxTrunc + 1];   // A^0 .. A^kMaxTrunc
   long long spin_cycles; // bounded wait of the grid barrier
 };
 
@@ -85,6 +84,7 @@ struct BoundaryArgs {
   cd* etab;
   cd* phitab;
   cd* rowscal;
+  cd* detab;             // nt + D entries, see k_detab
   double* norms;         // norms[0] is set here (row 0 is the initial condition)
   int64_t nt, nphi;
   int D;
@@ -110,13 +110,15 @@ struct fdtd_plan_s {
   // workspace layout (byte offsets)
   size_t ws_need;
   char* ws;
-  size_t off_sync, off_etab, off_phi, off_rowscal, off_norms, off_hscr, off_partials, off_colsplit, off_ring, off_snaps;
+  size_t off_sync, off_etab, off_phi, off_rowscal, off_detab, off_norms, off_hscr, off_partials, off_colsplit, off_ring, off_snaps;
   int64_t stride, nphi, nsnap;
   int R;
   size_t elem;
   int64_t rows_done;     // rows available (0 before set_boundary)
   int state;             // 0 planned, 1 bound, 2 boundary set
-  int kscan, kfix, khalo;
+  int kfix, khalo;
+  size_t march_smem;     // dynamic shared memory of the march (delay pair sums)
+  int mid_weight;        // column split weight of -a < x <= 3a
   bool record_errors = true;  // false: keep no message (no host allocation on error paths)
   std::string last_error;
 };
@@ -129,6 +131,6 @@ namespace fdtd {
 // launchers (return cudaError_t)
 cudaError_t launch_boundary(const BoundaryArgs& a, cd* hscratch, bool compute_etable, cudaStream_t s);
 cudaError_t launch_gamma_star(const int32_t* n, const double* z, double* out, int64_t count, cudaStream_t s);
-cudaError_t launch_march_f64(const MarchArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_march_f64(const MarchArgs& a, int grid, size_t smem, cudaStream_t s);
 int march_f64_max_grid(int device);
 }  // namespace fdtd

@@ -11,28 +11,34 @@
 //
 // Everything except c2 psi[n][m-1] depends on earlier rows only, so a row is
 // r_m (parallel over m) followed by the first-order recurrence
-// y_m = c2 y_{m-1} + r_m.  |c2| = |W delta| / |4 + W delta| < 1, so the
-// influence of a carry dies as |c2|^k; the recurrence is evaluated exactly
-// where that influence exceeds 2^-60 and truncated beyond.
+// y_m = c2 y_{m-1} + r_m.  |c2| = |W delta| / |4 + W delta| < 1, so a carry's
+// influence dies as |c2|^k; the recurrence is carried exactly while that
+// influence exceeds 2^-60 (kfix columns) and truncated beyond, which is below
+// FP64 rounding.
 //
-// Work layout: one persistent cooperative CTA per SM; CTA b owns the columns
-// [colsplit[b], colsplit[b+1]) of every row and sweeps them in chunks of
-// 512 threads x 4 consecutive columns.  Inside a chunk each thread runs the
-// recurrence over its 4 columns from zero, then takes its carry from the
-// previous threads' last values (kscan terms), then adds c2^(v+1) carry to
-// its first kfix columns.  The carry into a CTA's first column is the
-// recurrence run over khalo columns to its left (or the exact boundary value
-// psi(-a, t) for the first CTA).  A grid-wide barrier with a bounded wait
-// separates rows: every read of row n-1, n-D and n-D-1 is then complete.
+// Work layout: one persistent cooperative CTA per SM.  CTA b owns the columns
+// [colsplit[b], colsplit[b+1]) of every row; each of its threads owns one
+// contiguous segment of them.  Per row a thread runs the recurrence over its
+// segment from a zero carry, keeping the first kMarchP columns in registers
+// and storing the rest (exact once kfix columns have passed).  After a CTA
+// barrier the thread takes its carry from the local last values of the
+// threads before it, adds c2^(v+1) carry to its first kfix columns, and
+// stores them.  The carry into a CTA's first column is the recurrence run over
+// khalo columns to its left (the exact boundary value psi(-a, t) for the first
+// CTA).  A grid-wide barrier with a bounded wait separates rows, so every read
+// of rows n-1, n-D and n-D-1 is complete.
+//
+// The delay term needs psi[n-D][m-D-1] + psi[n-D][m-D] and the same pair on
+// row n-D-1; the latter is the former of the previous row, so each column's
+// pair sum is kept in shared memory from one row to the next.
 //
 // Reads of x <= -a use psi(x,t) = C phi(x-t) e(t) from the boundary tables.
 // Beyond x > 3a every mirror read of lines 2-3 lands in x <= -a, and the
-// sources collapse to R1(n) (E(r2) - E(r3)) + R2(n) phi(r2), with
-// r2 = n - m - D/2, r3 = r2 + D and E(r) = theta(r) e(r delta).
+// sources collapse to R1(n) [E(r2) - E(r2+D)] + R2(n) phi(r2), r2 = n - m - D/2,
+// E(r) = theta(r) e(r delta), with the bracket tabulated (detab).
 //
 // The ring holds D+2 rows (slot n % (D+2)); loads of ring rows written in this
 // launch bypass L1 (ld.global.cg).
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "fdtd_internal.cuh"
@@ -41,6 +47,12 @@ namespace fdtd {
 
 __device__ __forceinline__ cd ldcg(const cd* p) {
   double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return cd{v.x, v.y};
+}
+// ring rows written before the last grid barrier: cached in L1 (the barrier's
+// acquire fence discards stale lines, as after a grid-wide sync)
+__device__ __forceinline__ cd ldring(const cd* p) {
+  double2 v = __ldca(reinterpret_cast<const double2*>(p));
   return cd{v.x, v.y};
 }
 __device__ __forceinline__ cd ldro(const cd* p) {
@@ -57,12 +69,14 @@ __device__ __forceinline__ cd psi_left(const MarchArgs& A, int64_t r, int64_t c)
   return A.C * (ldro(&A.phitab[r - c - Dh]) * ldro(&A.etab[r]));
 }
 
-// psi at any earlier point the update reads (rows n-D-1 .. n-1, or the current
-// row for columns left of -a)
-__device__ __forceinline__ cd psi_any(const MarchArgs& A, int64_t r, int64_t c) {
+// psi at any earlier point the update of row n reads (rows n-D-1 .. n-1, or
+// row n itself for columns left of -a); nslot = n % R
+__device__ __forceinline__ cd psi_any(const MarchArgs& A, int64_t n, int nslot, int64_t r, int64_t c) {
   const int Dh = A.D >> 1;
   if (c <= -Dh) return psi_left(A, r, c);
-  return ldcg(&A.ring[(r % A.R) * A.stride + (c + Dh - 1)]);
+  int slot = nslot - (int)(n - r);
+  if (slot < 0) slot += A.R;
+  return ldcg(&A.ring[(int64_t)slot * A.stride + (c + Dh - 1)]);
 }
 
 __device__ __forceinline__ cd e_theta(const MarchArgs& A, int64_t r) {
@@ -73,21 +87,21 @@ __device__ __forceinline__ cd e_theta(const MarchArgs& A, int64_t r) {
 
 // r_m for a column of the region -a < x <= 3a (m <= 3D/2): every term read
 // through psi_any.
-__device__ cd rhs_general(const MarchArgs& A, int64_t n, int64_t j, cd R2) {
+__device__ __noinline__ cd rhs_general(const MarchArgs& A, int64_t n, int nslot, int64_t j, cd R2) {
   const int D = A.D, Dh = D >> 1;
   const int64_t m = j - Dh + 1;
-  cd r = A.c1 * psi_any(A, n - 1, m - 1);
-  r = cfma(A.c2, psi_any(A, n - 1, m), r);
+  cd r = A.c1 * psi_any(A, n, nslot, n - 1, m - 1);
+  r = cfma(A.c2, psi_any(A, n, nslot, n - 1, m), r);
   if (n >= D + 1) {
-    cd sq = psi_any(A, n - D, m - D) + psi_any(A, n - D, m - D - 1) + psi_any(A, n - D - 1, m - D) +
-            psi_any(A, n - D - 1, m - D - 1);
+    cd sq = psi_any(A, n, nslot, n - D, m - D) + psi_any(A, n, nslot, n - D, m - D - 1) +
+            psi_any(A, n, nslot, n - D - 1, m - D) + psi_any(A, n, nslot, n - D - 1, m - D - 1);
     r = cfma(A.c3, sq, r);
   }
   const int64_t r2 = n - m - Dh;  // line 2: t - x - a at the centre
   if (r2 >= 0) {
     double w = (r2 == 0) ? 0.5 : 1.0;
-    cd bl = psi_any(A, r2, -m - D) + psi_any(A, r2, -m - D + 1);
-    cd br = psi_any(A, r2, -m) + psi_any(A, r2, -m + 1);
+    cd bl = psi_any(A, n, nslot, r2, -m - D) + psi_any(A, n, nslot, r2, -m - D + 1);
+    cd br = psi_any(A, n, nslot, r2, -m) + psi_any(A, n, nslot, r2, -m + 1);
     r = cfma(A.gs, w * (bl - br), r);
     r = cfma(R2, ldro(&A.phitab[r2]), r);  // line 4: phi((m-n) delta) = phitab[r2]
   }
@@ -95,34 +109,63 @@ __device__ cd rhs_general(const MarchArgs& A, int64_t n, int64_t j, cd R2) {
     const int64_t r3 = n - m + Dh;
     if (r3 >= 0) {
       double w = (r3 == 0) ? 0.5 : 1.0;
-      cd bl = psi_any(A, r3, D - m) + psi_any(A, r3, D - m + 1);
-      cd br = psi_any(A, r3, -m) + psi_any(A, r3, -m + 1);
+      cd bl = psi_any(A, n, nslot, r3, D - m) + psi_any(A, n, nslot, r3, D - m + 1);
+      cd br = psi_any(A, n, nslot, r3, -m) + psi_any(A, n, nslot, r3, -m + 1);
       r = cfma(A.gs, w * (bl - br), r);
     }
   }
   return r;
 }
 
+struct RowCtx {
+  int64_t n;
+  int nslot;        // n % R
+  const cd* row1;   // row n-1
+  const cd* rowD;   // row n-D (null if n < D)
+  const cd* rowD1;  // row n-D-1 (null if n < D+1)
+  cd* row0;         // row n
+  cd* snap;         // snapshot row or null
+  cd R1, R2;
+  cd* hs;           // shared pair sums (null: no reuse), indexed j - hbase
+  int64_t hbase;
+  bool cold;        // first row of this launch: pair sums not yet in shared memory
+};
+
 // r_m for x > 3a (j >= 2D).
-__device__ __forceinline__ cd rhs_bulk(const MarchArgs& A, int64_t n, int64_t j, const cd* row1, const cd* rowD,
-                                       const cd* rowD1, cd R1, cd R2) {
+__device__ __forceinline__ cd rhs_bulk(const MarchArgs& A, const RowCtx& R, int64_t j) {
   const int D = A.D;
-  cd r = A.c1 * ldcg(row1 + j - 1);
-  r = cfma(A.c2, ldcg(row1 + j), r);
-  if (rowD1) {
-    cd sq = ldcg(rowD + j - D) + ldcg(rowD + j - D - 1) + ldcg(rowD1 + j - D) + ldcg(rowD1 + j - D - 1);
-    r = cfma(A.c3, sq, r);
+  cd r = A.c1 * ldring(R.row1 + j - 1);
+  r = cfma(A.c2, ldring(R.row1 + j), r);
+  if (R.rowD) {
+    cd hn = ldring(R.rowD + j - D - 1) + ldring(R.rowD + j - D);  // row n-D pair
+    if (R.rowD1) {
+      cd hp;
+      if (R.hs && !R.cold) hp = R.hs[j - R.hbase];
+      else hp = ldring(R.rowD1 + j - D - 1) + ldring(R.rowD1 + j - D);
+      r = cfma(A.c3, hn + hp, r);
+    }
+    if (R.hs) R.hs[j - R.hbase] = hn;
   }
-  const int64_t r2 = n - j - 1;  // n - m - D/2 with m = j - D/2 + 1
-  r = cfma(R1, e_theta(A, r2) - e_theta(A, r2 + D), r);
-  if (r2 >= 0) r = cfma(R2, ldro(&A.phitab[r2]), r);
+  const int64_t i = R.n - j - 1 + D;  // r2 + D
+  if (i >= 0) {
+    r = cfma(R.R1, ldro(&A.detab[i]), r);
+    if (i >= D) r = cfma(R.R2, ldro(&A.phitab[i - D]), r);
+  }
   return r;
 }
 
-__device__ __forceinline__ cd rhs_any(const MarchArgs& A, int64_t n, int64_t j, const cd* row1, const cd* rowD,
-                                      const cd* rowD1, cd R1, cd R2) {
-  if (j >= 2 * (int64_t)A.D) return rhs_bulk(A, n, j, row1, rowD, rowD1, R1, R2);
-  return rhs_general(A, n, j, R2);
+__device__ __forceinline__ cd rhs_any(const MarchArgs& A, const RowCtx& R, int64_t j) {
+  if (j >= 2 * (int64_t)A.D) return rhs_bulk(A, R, j);
+  return rhs_general(A, R.n, R.nslot, j, R.R2);
+}
+
+// store a final value of row n and add |y|^2 to the norm (the trapezoid's
+// half weight at the last column is applied once, by the CTA that owns it)
+__device__ __forceinline__ void finalize(const RowCtx& R, int64_t j, cd y, double& nacc) {
+  stcg(R.row0 + j, y);
+  if (R.snap) stcg(R.snap + j, y);
+  nacc = fma(y.re, y.re, nacc);
+  nacc = fma(y.im, y.im, nacc);
 }
 
 // Grid-wide barrier with a bounded wait.  Returns false if any CTA has
@@ -160,8 +203,10 @@ __device__ bool grid_barrier(SyncWords* s, long long spin_cycles, int64_t row) {
 }
 
 __global__ void __launch_bounds__(kMarchThreads, 1) k_march_f64(const MarchArgs A) {
-  constexpr int V = kMarchV;
+  constexpr int P = kMarchP;
+  extern __shared__ cd s_h[];  // pair sums, khalo + CTA range entries
   __shared__ cd s_last[kMarchThreads];
+  __shared__ int s_len[kMarchThreads];
   __shared__ cd s_carry;
   __shared__ cd s_halo[kMaxTrunc];
   __shared__ double s_red[kMarchThreads / 32];
@@ -169,78 +214,103 @@ __global__ void __launch_bounds__(kMarchThreads, 1) k_march_f64(const MarchArgs 
   const int tid = threadIdx.x;
   const int D = A.D, Dh = D >> 1;
   const int64_t j_lo = A.colsplit[blockIdx.x], j_hi = A.colsplit[blockIdx.x + 1];
-  const int64_t nx = A.nx;
+  // This thread's segment [s0, s1).  A CTA inside x > 3a splits its range into
+  // equal odd-length segments (the 16-byte pair sums of the 8 threads of a
+  // shared-memory phase then fall in distinct banks).  A CTA that holds
+  // columns of -a < x <= 3a splits by cost instead, a column there counting
+  // mid_weight columns of the bulk, so that no thread is left with most of it.
+  const int64_t G2 = (2 * (int64_t)D < A.nx) ? 2 * (int64_t)D : A.nx;
+  int64_t s0, s1;
+  if (j_lo >= G2) {
+    const int64_t seg = ((j_hi - j_lo + kMarchThreads - 1) / kMarchThreads) | 1;
+    s0 = j_lo + (int64_t)tid * seg;
+    if (s0 > j_hi) s0 = j_hi;
+    s1 = (s0 + seg < j_hi) ? s0 + seg : j_hi;
+  } else {
+    const int64_t wm = A.mid_weight;
+    auto cumw = [&](int64_t j) { return j <= G2 ? wm * j : wm * G2 + (j - G2); };
+    auto inv = [&](int64_t x) { return x <= wm * G2 ? (x + wm - 1) / wm : G2 + (x - wm * G2); };
+    const int64_t W0 = cumw(j_lo), W1 = cumw(j_hi);
+    s0 = inv(W0 + (W1 - W0) * tid / kMarchThreads);
+    s1 = inv(W0 + (W1 - W0) * (tid + 1) / kMarchThreads);
+  }
+  const int64_t h0 = (j_lo - A.khalo > 0) ? j_lo - A.khalo : 0;  // first halo column
+  const int nh = (int)(j_lo - h0);
+  s_len[tid] = (int)(s1 - s0);
+  __syncthreads();
 
   for (int64_t n = A.n_begin; n < A.n_end; ++n) {
-    const cd* row1 = A.ring + ((n - 1) % A.R) * A.stride;
-    const cd* rowD = (n >= D) ? A.ring + ((n - D) % A.R) * A.stride : nullptr;
-    const cd* rowD1 = (n >= D + 1) ? A.ring + ((n - D - 1) % A.R) * A.stride : nullptr;
-    cd* row0 = A.ring + (n % A.R) * A.stride;
-    const cd R1 = ldro(&A.rowscal[2 * n]), R2 = ldro(&A.rowscal[2 * n + 1]);
-    cd* snap = (A.snaps && A.tstep >= 0 && n % (A.tstep + 1) == 0) ? A.snaps + (n / (A.tstep + 1)) * nx : nullptr;
+    RowCtx R;
+    R.n = n;
+    R.nslot = (int)(n % A.R);
+    R.row1 = A.ring + ((n - 1) % A.R) * A.stride;
+    R.rowD = (n >= D) ? A.ring + ((n - D) % A.R) * A.stride : nullptr;
+    R.rowD1 = (n >= D + 1) ? A.ring + ((n - D - 1) % A.R) * A.stride : nullptr;
+    R.row0 = A.ring + (n % A.R) * A.stride;
+    R.snap = (A.snaps && A.tstep >= 0 && n % (A.tstep + 1) == 0) ? A.snaps + (n / (A.tstep + 1)) * A.nx : nullptr;
+    R.R1 = ldro(&A.rowscal[2 * n]);
+    R.R2 = ldro(&A.rowscal[2 * n + 1]);
+    R.hs = A.hreuse ? s_h : nullptr;
+    R.hbase = h0;
+    R.cold = (n == A.n_begin);
 
     // carry into column j_lo: the true psi[n][j_lo - 1]
-    if (j_lo < j_hi) {
-      const int64_t h0 = (j_lo - A.khalo > 0) ? j_lo - A.khalo : 0;
-      const int nh = (int)(j_lo - h0);
-      if (tid < 32) {
-        for (int c = tid; c < nh; c += 32) s_halo[c] = rhs_any(A, n, h0 + c, row1, rowD, rowD1, R1, R2);
-        __syncwarp();
-        if (tid == 0) {
-          cd y = (h0 == 0) ? psi_left(A, n, -Dh) : cd{0.0, 0.0};
-          for (int c = 0; c < nh; ++c) y = cfma(A.c2, y, s_halo[c]);
-          s_carry = y;
-        }
+    if (tid < 32 && j_lo < j_hi) {
+      for (int c = tid; c < nh; c += 32) s_halo[c] = rhs_any(A, R, h0 + c);
+      __syncwarp();
+      if (tid == 0) {
+        cd y = (h0 == 0) ? psi_left(A, n, -Dh) : cd{0.0, 0.0};
+        for (int c = 0; c < nh; ++c) y = cfma(A.c2, y, s_halo[c]);
+        s_carry = y;
       }
     }
+
+    // pass A: the segment from a zero carry
+    double nacc = 0.0;
+    cd y0[P];
+    cd y = cd{0.0, 0.0};
+#pragma unroll
+    for (int v = 0; v < P; ++v) {
+      const int64_t j = s0 + v;
+      if (j < s1) y = cfma(A.c2, y, rhs_any(A, R, j));
+      y0[v] = y;
+    }
+    for (int64_t j = s0 + P; j < s1; ++j) {
+      y = cfma(A.c2, y, rhs_any(A, R, j));
+      if (j - s0 < A.kfix) stcg(R.row0 + j, y);  // provisional: receives the carry in pass B
+      else finalize(R, j, y, nacc);
+    }
+    s_last[tid] = (s0 < s1) ? y : cd{0.0, 0.0};
     __syncthreads();
 
-    double nacc = 0.0;
-    for (int64_t jc = j_lo; jc < j_hi; jc += kMarchChunk) {
-      const int64_t j0 = jc + (int64_t)tid * V;
-      cd y[V];
-      cd prev = cd{0.0, 0.0};
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const int64_t j = j0 + v;
-        cd r = (j < j_hi) ? rhs_any(A, n, j, row1, rowD, rowD1, R1, R2) : cd{0.0, 0.0};
-        prev = cfma(A.c2, prev, r);
-        y[v] = prev;
-      }
-      s_last[tid] = y[V - 1];
-      __syncthreads();
-      // carry into this thread's first column
-      const cd carry0 = s_carry;
-      cd carry = cd{0.0, 0.0};
-      for (int s = 1; s <= A.kscan; ++s) {
+    // pass B: carry from the threads before, added to the first kfix columns.
+    // The true last value of thread u is b_u + c2^len_u (carry into u); unrolled
+    // back until the product of the c2^len factors drops below 2^-60.
+    if (s0 < s1) {
+      cd carry = cd{0.0, 0.0}, ap = cd{1.0, 0.0};
+      for (int s = 1; s <= tid + 1; ++s) {
         if (tid - s >= 0) {
-          carry = cfma(A.Apow[s - 1], s_last[tid - s], carry);
+          carry = cfma(ap, s_last[tid - s], carry);
+          const int lu = s_len[tid - s];
+          ap = ap * ((lu <= kMaxTrunc) ? A.c2pow[lu] : cd{0.0, 0.0});
+          if (cabs2(ap) < 7.5e-37) break;  // (2^-60)^2
         } else {
-          carry = cfma(A.Apow[s - 1], carry0, carry);
-          break;
+          carry = cfma(ap, s_carry, carry);
         }
       }
 #pragma unroll
-      for (int v = 0; v < V; ++v)
-        if (v < A.kfix) y[v] = cfma(A.c2pow[v + 1], carry, y[v]);
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const int64_t j = j0 + v;
-        if (j < j_hi) {
-          stcg(row0 + j, y[v]);
-          if (snap) stcg(snap + j, y[v]);
-          double p2 = cabs2(y[v]);
-          nacc += (j == nx - 1) ? 0.5 * p2 : p2;
+      for (int v = 0; v < P; ++v) {
+        const int64_t j = s0 + v;
+        if (j < s1) {
+          cd yv = (v < A.kfix) ? cfma(A.c2pow[v + 1], carry, y0[v]) : y0[v];
+          finalize(R, j, yv, nacc);
         }
       }
-      __syncthreads();  // all threads have read s_carry / s_last
-      const int64_t jlast = ((jc + kMarchChunk < j_hi) ? jc + kMarchChunk : j_hi) - 1;
-      if (jlast >= j0 && jlast < j0 + V) {
-#pragma unroll
-        for (int v = 0; v < V; ++v)
-          if (j0 + v == jlast) s_carry = y[v];
+      for (int v = P; v < A.kfix && s0 + v < s1; ++v) {
+        const int64_t j = s0 + v;
+        cd yv = cfma(A.c2pow[v + 1], carry, ldcg(R.row0 + j));
+        finalize(R, j, yv, nacc);
       }
-      __syncthreads();
     }
 
     // deterministic norm partial of this CTA
@@ -251,6 +321,7 @@ __global__ void __launch_bounds__(kMarchThreads, 1) k_march_f64(const MarchArgs 
     if (tid == 0) {
       double t = 0.0;
       for (int w = 0; w < kMarchThreads / 32; ++w) t += s_red[w];
+      if (j_hi == A.nx && j_lo < j_hi) t -= 0.5 * cabs2(ldcg(R.row0 + A.nx - 1));  // trapezoid end weight
       A.partials[(n & 1) * gridDim.x + blockIdx.x] = t;
     }
     if (!grid_barrier(A.sync, A.spin_cycles, n)) return;
@@ -270,9 +341,13 @@ int march_f64_max_grid(int device) {
   return sms * (per > 0 ? per : 0);
 }
 
-cudaError_t launch_march_f64(const MarchArgs& a, int grid, cudaStream_t s) {
+cudaError_t launch_march_f64(const MarchArgs& a, int grid, size_t smem, cudaStream_t s) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_march_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   void* args[] = {const_cast<MarchArgs*>(&a)};
-  return cudaLaunchCooperativeKernel((const void*)k_march_f64, dim3(grid), dim3(kMarchThreads), args, 0, s);
+  return cudaLaunchCooperativeKernel((const void*)k_march_f64, dim3(grid), dim3(kMarchThreads), args, smem, s);
 }
 
 }  // namespace fdtd
