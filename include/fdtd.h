@@ -113,7 +113,11 @@ enum {
 /*
  * fdtd_plan -- validate parameters and size the workspace.
  *   p            : array of n_instances parameter sets (host memory, read only;
- *                  copied).  This build supports n_instances == 1.
+ *                  copied).  FDTD_F64 plans hold one instance.  FDTD_F32_COMP
+ *                  plans hold 1 or more independent instances (each with its own
+ *                  nx, nt, D, physics and tstep; rows_per_launch is taken from
+ *                  p[0]); fdtd_march then advances every instance by n_rows in
+ *                  one persistent launch, a thread-block cluster per instance.
  *   cuda_stream  : cudaStream_t the plan queues its work on (NULL = default).
  *   workspace_bytes (out): device bytes the caller must lend (256-byte aligned).
  *   out (out)    : new plan handle, released by fdtd_destroy.
@@ -163,6 +167,18 @@ fdtd_status fdtd_readout(fdtd_plan_t plan, int32_t kind, void* dst, int64_t dst_
 
 /* Size in bytes that fdtd_readout(kind) writes at the current state. */
 int64_t fdtd_readout_bytes(fdtd_plan_t plan, int32_t kind);
+
+/*
+ * fdtd_readout_instance -- fdtd_readout for instance `instance` of a plan made
+ * with n_instances > 1 (instance 0 is what fdtd_readout returns).  For a
+ * FDTD_BOUNDARY_TABLE source of a batched plan, device_table holds the
+ * instances' tables one after another (sum of nt complex128 values).
+ * Errors: FDTD_ERR_INVALID_ARG (instance out of range), as fdtd_readout.
+ */
+fdtd_status fdtd_readout_instance(fdtd_plan_t plan, int32_t instance, int32_t kind, void* dst, int64_t dst_bytes);
+
+/* Size in bytes that fdtd_readout_instance(instance, kind) writes; -1 if invalid. */
+int64_t fdtd_readout_instance_bytes(fdtd_plan_t plan, int32_t instance, int32_t kind);
 
 /* fdtd_destroy -- release the host-side plan (not the workspace). NULL is a no-op. */
 void fdtd_destroy(fdtd_plan_t plan);

@@ -1,0 +1,339 @@
+// batch_api.cu -- host side of complex64 plans (FDTD_F32_COMP): one instance or
+// a batch of independent instances marched by one persistent cluster launch.
+// The boundary of every instance is built by the FP64 kernels of boundary.cu;
+// the march reads FP32 copies of its tables.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "fdtd_internal.cuh"
+
+using fdtd::cd;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+cd cdiv(cd a, cd b) {
+  double d = b.re * b.re + b.im * b.im;
+  return cd{(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+
+fdtd_status fail(fdtd_plan_s* p, fdtd_status s, const char* msg) {
+  if (p && p->record_errors) p->last_error = msg;
+  return s;
+}
+fdtd_status cuda_fail(fdtd_plan_s* p, cudaError_t e, const char* where) {
+  if (p && p->record_errors) {
+    p->last_error = where;
+    p->last_error += ": ";
+    p->last_error += cudaGetErrorString(e);
+  }
+  return FDTD_ERR_CUDA;
+}
+
+constexpr int kMidWeight = 16;
+
+// columns of CTA `rank` of `C`, as the kernel splits them (cost-weighted)
+void cta_range_host(int64_t nx, int D, int rank, int C, int64_t* lo, int64_t* hi) {
+  const int64_t G2 = std::min<int64_t>(2 * (int64_t)D, nx);
+  const int64_t wm = kMidWeight;
+  const int64_t W = wm * G2 + (nx - G2);
+  auto inv = [&](int64_t x) { return x <= wm * G2 ? (x + wm - 1) / wm : G2 + (x - wm * G2); };
+  *lo = inv(W * rank / C);
+  *hi = inv(W * (rank + 1) / C);
+}
+
+fdtd_status validate(const fdtd_params& p) {
+  if (p.struct_size != sizeof(fdtd_params)) return FDTD_ERR_INVALID_ARG;
+  if (p.D < 2 || (p.D & 1) || p.nx < p.D || p.nt < 1) return FDTD_ERR_INVALID_ARG;
+  if (!(p.delta > 0) || !(p.gamma > 0) || !isfinite(p.omega0) || !isfinite(p.k)) return FDTD_ERR_INVALID_ARG;
+  if (p.init_cond < FDTD_IC_STIM_EMISSION || p.init_cond > FDTD_IC_TWO_PHOTON_GAUSS) return FDTD_ERR_INVALID_ARG;
+  if (p.init_cond != FDTD_IC_TWO_PHOTON_GAUSS && !(p.alpha > 0)) return FDTD_ERR_INVALID_ARG;
+  if (p.init_cond == FDTD_IC_TWO_PHOTON_GAUSS && !(p.sigma > 0)) return FDTD_ERR_INVALID_ARG;
+  if (p.tstep < -1 || p.rows_per_launch < 0) return FDTD_ERR_INVALID_ARG;
+  if (p.precision != FDTD_F32_COMP) return FDTD_ERR_INVALID_ARG;
+  return FDTD_OK;
+}
+
+template <class T>
+T* at(fdtd_plan_s* P, size_t off) {
+  return reinterpret_cast<T*>(P->ws + off);
+}
+
+}  // namespace
+
+fdtd_status batch_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n, void* cuda_stream,
+                            size_t* workspace_bytes) {
+  if (n < 1) return FDTD_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    fdtd_status st = validate(pin[i]);
+    if (st != FDTD_OK) return st;
+  }
+  P->batched = true;
+  P->p = pin[0];
+  P->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  if (cudaGetDevice(&P->device) != cudaSuccess) return FDTD_ERR_CUDA;
+  cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
+  P->record_errors = true;
+  P->inst.assign(n, fdtd_batch_inst{});
+  // cluster size: enough CTAs that the widest instance gives each thread a few columns
+  int64_t maxnx = 0;
+  for (int i = 0; i < n; ++i) maxnx = std::max<int64_t>(maxnx, pin[i].nx);
+  int cs = 1;
+  while (cs < 8 && (int64_t)cs * fdtd::kF32Threads * 4 < maxnx) cs *= 2;
+  P->csize = cs;
+
+  size_t off = 0;
+  P->off_sync = off;  off = align_up(off + sizeof(fdtd::SyncWords));
+  P->off_desc = off;  off = align_up(off + sizeof(fdtd::InstDesc) * (size_t)n);
+  P->off_order = off; off = align_up(off + sizeof(int) * (size_t)n);
+  P->off_queue = off; off = align_up(off + sizeof(unsigned int) * 4);
+  int64_t cols = 0;
+  for (int i = 0; i < n; ++i) {
+    const fdtd_params& p = pin[i];
+    fdtd_batch_inst& b = P->inst[i];
+    b.p = p;
+    const cd W = cd{0.5 * p.gamma, p.omega0};
+    const cd A = cd{1.0 / p.delta + W.re / 4.0, W.im / 4.0};
+    const cd B = cd{1.0 / p.delta - W.re / 4.0, -W.im / 4.0};
+    b.cs = cdiv(cd{1.0, 0.0}, A);
+    b.c1 = cdiv(B, A);
+    b.c2 = cdiv(cd{-W.re / 4.0, -W.im / 4.0}, A);
+    b.c3 = (p.gamma / 8.0) * b.cs;
+    b.gs = (-p.gamma / 4.0) * b.cs;
+    b.C = (p.init_cond == FDTD_IC_STIM_EMISSION) ? 1.0 : sqrt(2.0);
+    // carry depth at FP32 rounding: |c2|^k < 2^-26
+    const double ac2 = hypot(b.c2.re, b.c2.im);
+    int k = (ac2 <= 0) ? 1 : (int)ceil(-26.0 * log(2.0) / log(ac2));
+    if (k < 1) k = 1;
+    if (ac2 >= 1.0 || k > fdtd::kF32MaxTrunc) return FDTD_ERR_UNSUPPORTED;
+    b.kfix = k;
+    b.khalo = k;
+    b.R = p.D + 2;
+    b.stride = (p.nx + 63) / 64 * 64 + 64;  // complex64 row pitch, never a power of two apart
+    b.nphi = p.nt + 3 * (int64_t)p.D + 8;
+    b.nsnap = (p.tstep >= 0) ? (p.nt - 1) / (p.tstep + 1) + 1 : 0;
+    int64_t cm = 0;
+    for (int r = 0; r < cs; ++r) {
+      int64_t lo, hi;
+      cta_range_host(p.nx, p.D, r, cs, &lo, &hi);
+      cm = std::max(cm, hi - lo);
+    }
+    b.cols_max = cm + b.khalo;
+    cols = std::max(cols, b.cols_max);
+    b.off_etab = off;     off = align_up(off + sizeof(cd) * (size_t)p.nt);
+    b.off_phi = off;      off = align_up(off + sizeof(cd) * (size_t)b.nphi);
+    b.off_rowscal = off;  off = align_up(off + 2 * sizeof(cd) * (size_t)p.nt);
+    b.off_detab = off;    off = align_up(off + sizeof(cd) * (size_t)(p.nt + p.D));
+    b.off_norms = off;    off = align_up(off + sizeof(double) * (size_t)p.nt);
+    b.off_hscr = off;     off = align_up(off + sizeof(cd) * (size_t)p.nt);
+    b.off_etab32 = off;   off = align_up(off + sizeof(float2) * (size_t)p.nt);
+    b.off_phi32 = off;    off = align_up(off + sizeof(float2) * (size_t)b.nphi);
+    b.off_rowscal32 = off; off = align_up(off + 2 * sizeof(float2) * (size_t)p.nt);
+    b.off_detab32 = off;  off = align_up(off + sizeof(float2) * (size_t)(p.nt + p.D));
+    b.off_lo = off;       off = align_up(off + sizeof(float2) * (size_t)p.nx);
+    b.off_edge = off;     off = align_up(off + sizeof(float2) * 2 * fdtd::kClusterMax);
+    b.off_part = off;     off = align_up(off + sizeof(double) * 2 * fdtd::kClusterMax);
+    b.off_ring = off;     off = align_up(off + sizeof(float2) * (size_t)b.R * (size_t)b.stride);
+    b.off_snaps = off;    off = align_up(off + sizeof(float2) * (size_t)b.nsnap * (size_t)p.nx);
+    b.rows_done = 0;
+  }
+  P->smem_cols = cols;
+  const size_t smem = fdtd::march_f32c_smem(cols);
+  if (smem + 16 * 1024 > 227 * 1024) return FDTD_ERR_UNSUPPORTED;  // instance too wide for the cluster
+  int maxc = fdtd::march_f32c_max_clusters(P->csize, smem);
+  if (maxc <= 0) return FDTD_ERR_CUDA;
+  P->nclusters = std::min(maxc, n);
+  P->ws_need = off;
+  P->state = 0;
+  *workspace_bytes = off;
+  return FDTD_OK;
+}
+
+fdtd_status batch_set_boundary(fdtd_plan_s* P, int32_t source, const void* table, int64_t ntab) {
+  const int n = (int)P->inst.size();
+  if (source != FDTD_BOUNDARY_ANALYTIC && source != FDTD_BOUNDARY_TABLE)
+    return fail(P, FDTD_ERR_INVALID_ARG, "unknown boundary source");
+  int64_t total_nt = 0;
+  for (auto& b : P->inst) total_nt += b.p.nt;
+  if (source == FDTD_BOUNDARY_TABLE && (!table || ntab != total_nt))
+    return fail(P, FDTD_ERR_INVALID_ARG, "boundary table must hold sum(nt) complex128 values");
+  cudaStream_t s = P->stream;
+  cudaError_t e = cudaMemsetAsync(P->ws + P->off_sync, 0, sizeof(fdtd::SyncWords), s);
+  if (e != cudaSuccess) return cuda_fail(P, e, "cudaMemsetAsync");
+  std::vector<fdtd::InstDesc> desc(n);
+  const char* tab = static_cast<const char*>(table);
+  for (int i = 0; i < n; ++i) {
+    fdtd_batch_inst& b = P->inst[i];
+    const fdtd_params& p = b.p;
+    e = cudaMemsetAsync(P->ws + b.off_ring, 0, sizeof(float2) * (size_t)b.R * (size_t)b.stride, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->ws + b.off_norms, 0, sizeof(double) * (size_t)p.nt, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->ws + b.off_lo, 0, sizeof(float2) * (size_t)p.nx, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->ws + b.off_edge, 0, sizeof(float2) * 2 * fdtd::kClusterMax, s);
+    if (e == cudaSuccess && b.nsnap)
+      e = cudaMemsetAsync(P->ws + b.off_snaps, 0, sizeof(float2) * (size_t)b.nsnap * (size_t)p.nx, s);
+    if (e != cudaSuccess) return cuda_fail(P, e, "cudaMemsetAsync");
+    if (source == FDTD_BOUNDARY_TABLE) {
+      e = cudaMemcpyAsync(P->ws + b.off_etab, tab, sizeof(cd) * (size_t)p.nt, cudaMemcpyDeviceToDevice, s);
+      tab += sizeof(cd) * (size_t)p.nt;
+      if (e != cudaSuccess) return cuda_fail(P, e, "cudaMemcpyAsync(table)");
+    }
+    fdtd::BoundaryArgs a;
+    a.etab = at<cd>(P, b.off_etab);
+    a.phitab = at<cd>(P, b.off_phi);
+    a.rowscal = at<cd>(P, b.off_rowscal);
+    a.detab = at<cd>(P, b.off_detab);
+    a.norms = at<double>(P, b.off_norms);
+    a.nt = p.nt;
+    a.nphi = b.nphi;
+    a.D = p.D;
+    a.init_cond = p.init_cond;
+    a.delta = p.delta;
+    a.gamma = p.gamma;
+    a.omega0 = p.omega0;
+    a.k = p.k;
+    a.alpha = p.alpha;
+    a.sigma = p.sigma;
+    a.center = p.center;
+    a.C = b.C;
+    a.cs = b.cs;
+    a.status = &at<fdtd::SyncWords>(P, P->off_sync)->status;
+    e = fdtd::launch_boundary(a, at<cd>(P, b.off_hscr), source == FDTD_BOUNDARY_ANALYTIC, s);
+    if (e != cudaSuccess) return cuda_fail(P, e, "boundary kernels");
+
+    fdtd::InstDesc& d = desc[i];
+    memset(&d, 0, sizeof d);
+    d.nx = p.nx;
+    d.nt = p.nt;
+    d.stride = b.stride;
+    d.nphi = b.nphi;
+    d.range[0] = 1;
+    d.range[1] = 1;
+    d.smem_cols = P->smem_cols;
+    d.D = p.D;
+    d.R = b.R;
+    d.kfix = b.kfix;
+    d.khalo = b.khalo;
+    d.mid_weight = kMidWeight;
+    d.tstep = p.tstep;
+    auto f = [](cd v) { return make_float2((float)v.re, (float)v.im); };
+    d.d1 = f(cd{b.c1.re - 1.0, b.c1.im});
+    d.c2 = f(b.c2);
+    d.c3 = f(b.c3);
+    d.gs = f(b.gs);
+    cd pw = cd{1.0, 0.0};
+    for (int k = 0; k <= fdtd::kF32MaxTrunc; ++k) {
+      d.c2pow[k] = f(pw);
+      pw = pw * b.c2;
+    }
+    d.C = b.C;
+    d.delta = p.delta;
+    d.ring = at<float2>(P, b.off_ring);
+    d.snaps = b.nsnap ? at<float2>(P, b.off_snaps) : nullptr;
+    d.lo_g = at<float2>(P, b.off_lo);
+    d.lo_edge = at<float2>(P, b.off_edge);
+    d.partials = at<double>(P, b.off_part);
+    d.norms = at<double>(P, b.off_norms);
+    d.etab = at<cd>(P, b.off_etab);
+    d.phitab = at<cd>(P, b.off_phi);
+    d.etab32 = at<float2>(P, b.off_etab32);
+    d.phitab32 = at<float2>(P, b.off_phi32);
+    d.detab32 = at<float2>(P, b.off_detab32);
+    d.rowscal32 = at<float2>(P, b.off_rowscal32);
+    e = fdtd::launch_tables32(d, at<cd>(P, b.off_detab), at<cd>(P, b.off_rowscal), s);
+    if (e != cudaSuccess) return cuda_fail(P, e, "tables32");
+    b.rows_done = 1;
+  }
+  // queue order: largest instances first
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return P->inst[x].p.nx * P->inst[x].p.nt > P->inst[y].p.nx * P->inst[y].p.nt;
+  });
+  e = cudaMemcpyAsync(P->ws + P->off_desc, desc.data(), sizeof(fdtd::InstDesc) * (size_t)n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(P->ws + P->off_order, order.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(P, e, "cudaMemcpyAsync(descriptors)");
+  // the pageable copies above are staged before they return
+  P->rows_done = 1;
+  P->state = 2;
+  return FDTD_OK;
+}
+
+fdtd_status batch_march(fdtd_plan_s* P, int64_t rows) {
+  const int n = (int)P->inst.size();
+  int64_t maxleft = 0;
+  for (auto& b : P->inst) maxleft = std::max<int64_t>(maxleft, b.p.nt - b.rows_done);
+  if (rows > maxleft) rows = maxleft;
+  if (rows <= 0) return FDTD_OK;
+  const int64_t per = P->p.rows_per_launch > 0 ? P->p.rows_per_launch : 4096;
+  cudaStream_t s = P->stream;
+  const size_t smem = fdtd::march_f32c_smem(P->smem_cols);
+  for (int64_t done = 0; done < rows; done += per) {
+    const int64_t step = std::min<int64_t>(per, rows - done);
+    cudaError_t e = fdtd::launch_advance(at<fdtd::InstDesc>(P, P->off_desc), n, step, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->ws + P->off_queue, 0, sizeof(unsigned int), s);
+    if (e == cudaSuccess)
+      e = fdtd::launch_march_f32c(at<fdtd::InstDesc>(P, P->off_desc), at<int>(P, P->off_order), n,
+                                  at<unsigned int>(P, P->off_queue), at<fdtd::SyncWords>(P, P->off_sync),
+                                  P->nclusters, P->csize, smem, s);
+    if (e != cudaSuccess) return cuda_fail(P, e, "march_f32c launch");
+  }
+  for (auto& b : P->inst) b.rows_done = std::min<int64_t>(b.p.nt, b.rows_done + rows);
+  P->rows_done = P->inst[0].rows_done;
+  return FDTD_OK;
+}
+
+int64_t batch_readout_bytes(fdtd_plan_s* P, int32_t i, int32_t kind) {
+  if (i < 0 || i >= (int)P->inst.size()) return -1;
+  const fdtd_batch_inst& b = P->inst[i];
+  switch (kind) {
+    case FDTD_READ_ROW: return (int64_t)sizeof(float2) * b.p.nx;
+    case FDTD_READ_NORMS: return (int64_t)sizeof(double) * b.rows_done;
+    case FDTD_READ_SNAPSHOTS: {
+      if (!b.nsnap || b.rows_done == 0) return 0;
+      int64_t ns = (b.rows_done - 1) / (b.p.tstep + 1) + 1;
+      return (int64_t)sizeof(float2) * ns * b.p.nx;
+    }
+    case FDTD_READ_ETABLE: return (int64_t)sizeof(cd) * b.p.nt;
+    case FDTD_READ_ROWS_DONE: return (int64_t)sizeof(int64_t);
+  }
+  return -1;
+}
+
+fdtd_status batch_readout(fdtd_plan_s* P, int32_t i, int32_t kind, void* dst, int64_t dst_bytes) {
+  int64_t need = batch_readout_bytes(P, i, kind);
+  if (need < 0) return fail(P, FDTD_ERR_INVALID_ARG, "unknown readout kind or instance");
+  if (!dst || dst_bytes < need) return fail(P, FDTD_ERR_INVALID_ARG, "readout destination missing or too small");
+  cudaError_t e = cudaStreamSynchronize(P->stream);
+  if (e != cudaSuccess) return cuda_fail(P, e, "cudaStreamSynchronize");
+  fdtd::SyncWords sw;
+  e = cudaMemcpy(&sw, P->ws + P->off_sync, sizeof sw, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(P, e, "cudaMemcpy(status)");
+  if (sw.status != 0) return fail(P, (fdtd_status)sw.status, "device latched an error");
+  const fdtd_batch_inst& b = P->inst[i];
+  const void* src = nullptr;
+  switch (kind) {
+    case FDTD_READ_ROW:
+      src = P->ws + b.off_ring + sizeof(float2) * (size_t)((b.rows_done - 1) % b.R) * (size_t)b.stride;
+      break;
+    case FDTD_READ_NORMS: src = P->ws + b.off_norms; break;
+    case FDTD_READ_SNAPSHOTS: src = P->ws + b.off_snaps; break;
+    case FDTD_READ_ETABLE: src = P->ws + b.off_etab; break;
+    case FDTD_READ_ROWS_DONE: memcpy(dst, &b.rows_done, sizeof(int64_t)); return FDTD_OK;
+  }
+  if (need > 0) {
+    e = cudaMemcpyAsync(dst, src, (size_t)need, cudaMemcpyDefault, P->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+    if (e != cudaSuccess) return cuda_fail(P, e, "cudaMemcpyAsync(readout)");
+  }
+  return FDTD_OK;
+}

@@ -154,7 +154,9 @@ fdtd_status fdtd_plan(const fdtd_params* pin, int32_t n_instances, void* cuda_st
   *out = nullptr;
   fdtd_plan_t P = new (std::nothrow) fdtd_plan_s();
   if (!P) return FDTD_ERR_INVALID_ARG;
-  fdtd_status st = fdtd_plan_fill(P, pin, n_instances, cuda_stream, workspace_bytes);
+  fdtd_status st = (pin->struct_size == sizeof(fdtd_params) && pin->precision == FDTD_F32_COMP)
+                       ? batch_plan_fill(P, pin, n_instances, cuda_stream, workspace_bytes)
+                       : fdtd_plan_fill(P, pin, n_instances, cuda_stream, workspace_bytes);
   if (st != FDTD_OK) {
     delete P;
     return st;
@@ -176,6 +178,7 @@ fdtd_status fdtd_bind_workspace(fdtd_plan_t P, void* device_ptr, size_t bytes) {
 fdtd_status fdtd_set_boundary(fdtd_plan_t P, int32_t source, const void* device_table, int64_t n) {
   if (!P) return FDTD_ERR_INVALID_ARG;
   if (P->state < 1) return fail(P, FDTD_ERR_STATE, "fdtd_set_boundary before fdtd_bind_workspace");
+  if (P->batched) return batch_set_boundary(P, source, device_table, n);
   const fdtd_params& p = P->p;
   if (source != FDTD_BOUNDARY_ANALYTIC && source != FDTD_BOUNDARY_TABLE)
     return fail(P, FDTD_ERR_INVALID_ARG, "unknown boundary source");
@@ -255,6 +258,7 @@ fdtd_status fdtd_march(fdtd_plan_t P, int64_t n_rows) {
   if (!P) return FDTD_ERR_INVALID_ARG;
   if (P->state < 2) return fail(P, FDTD_ERR_STATE, "fdtd_march before fdtd_set_boundary");
   if (n_rows < 0) return fail(P, FDTD_ERR_INVALID_ARG, "n_rows < 0");
+  if (P->batched) return batch_march(P, n_rows);
   const fdtd_params& p = P->p;
   int64_t end = P->rows_done + n_rows;
   if (end > p.nt) end = p.nt;
@@ -304,6 +308,7 @@ fdtd_status fdtd_march(fdtd_plan_t P, int64_t n_rows) {
 
 int64_t fdtd_readout_bytes(fdtd_plan_t P, int32_t kind) {
   if (!P) return -1;
+  if (P->batched) return batch_readout_bytes(P, 0, kind);
   const fdtd_params& p = P->p;
   switch (kind) {
     case FDTD_READ_ROW: return (int64_t)P->elem * p.nx;
@@ -322,6 +327,7 @@ int64_t fdtd_readout_bytes(fdtd_plan_t P, int32_t kind) {
 fdtd_status fdtd_readout(fdtd_plan_t P, int32_t kind, void* dst, int64_t dst_bytes) {
   if (!P) return FDTD_ERR_INVALID_ARG;
   if (P->state < 2) return fail(P, FDTD_ERR_STATE, "fdtd_readout before fdtd_set_boundary");
+  if (P->batched) return batch_readout(P, 0, kind, dst, dst_bytes);
   int64_t need = fdtd_readout_bytes(P, kind);
   if (need < 0) return fail(P, FDTD_ERR_INVALID_ARG, "unknown readout kind");
   if (!dst || dst_bytes < need) return fail(P, FDTD_ERR_INVALID_ARG, "readout destination missing or too small");
@@ -352,6 +358,22 @@ fdtd_status fdtd_readout(fdtd_plan_t P, int32_t kind, void* dst, int64_t dst_byt
   }
   (void)p;
   return FDTD_OK;
+}
+
+int64_t fdtd_readout_instance_bytes(fdtd_plan_t P, int32_t instance, int32_t kind) {
+  if (!P) return -1;
+  if (!P->batched) return instance == 0 ? fdtd_readout_bytes(P, kind) : -1;
+  return batch_readout_bytes(P, instance, kind);
+}
+
+fdtd_status fdtd_readout_instance(fdtd_plan_t P, int32_t instance, int32_t kind, void* dst, int64_t dst_bytes) {
+  if (!P) return FDTD_ERR_INVALID_ARG;
+  if (P->state < 2) return fail(P, FDTD_ERR_STATE, "fdtd_readout_instance before fdtd_set_boundary");
+  if (!P->batched) {
+    if (instance != 0) return fail(P, FDTD_ERR_INVALID_ARG, "instance out of range");
+    return fdtd_readout(P, kind, dst, dst_bytes);
+  }
+  return batch_readout(P, instance, kind, dst, dst_bytes);
 }
 
 void fdtd_destroy(fdtd_plan_t P) { delete P; }

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "fdtd.h"
 
@@ -39,6 +40,12 @@ constexpr int kMarchThreads = 512;   // threads per CTA of the FP64 march
 constexpr int kMarchP = 8;           // leading columns of a thread's segment kept in registers
 constexpr int kMaxTrunc = 64;        // cap on scan / halo truncation depth
 constexpr int kMaxGrid = 1024;       // cap on CTAs of the persistent march
+
+// complex64 compensated march (march_f32c.cu)
+constexpr int kF32Threads = 512;     // threads per CTA
+constexpr int kF32P = 8;             // leading columns of a segment kept in registers
+constexpr int kF32MaxTrunc = 16;     // |c2|^16 < 2^-26 required (|c2| < 0.32)
+constexpr int kClusterMax = 16;      // CTAs per cluster at most
 
 // sync words at the start of the workspace
 struct SyncWords {
@@ -95,7 +102,42 @@ struct BoundaryArgs {
   unsigned int* status;  // latched FDTD_ERR_NOT_CONVERGED
 };
 
+// one instance of a complex64 (batched) march, as the device reads it
+struct InstDesc {
+  int64_t nx, nt, stride, nphi;
+  int64_t range[2];        // rows [range[0], range[1]) marched by the current launch; range[1] = rows done
+  int64_t smem_cols;       // shared-memory columns per CTA available to the launch
+  int D, R, kfix, khalo, mid_weight, tstep;
+  float2 d1, c2, c3, gs;   // c1 - 1, c2, c3, -(Gamma/4)/A
+  float2 c2pow[kF32MaxTrunc + 1];
+  double C, delta;
+  float2* ring;            // R rows x stride complex64
+  float2* snaps;           // or null
+  float2* lo_g;            // nx: a_lo carried between launches
+  float2* lo_edge;         // 2 x kClusterMax: a_lo at CTA edges
+  double* partials;        // 2 x kClusterMax
+  double* norms;           // nt
+  const cd* etab;          // FP64 tables
+  const cd* phitab;
+  const float2* etab32;    // FP32 copies
+  const float2* phitab32;
+  const float2* detab32;
+  const float2* rowscal32;
+};
+
 }  // namespace fdtd
+
+// host mirror of one instance of a batched complex64 plan
+struct fdtd_batch_inst {
+  fdtd_params p;
+  size_t off_etab, off_phi, off_rowscal, off_detab, off_norms, off_hscr, off_etab32, off_phi32, off_rowscal32,
+      off_detab32, off_ring, off_snaps, off_lo, off_edge, off_part;
+  int64_t stride, nphi, nsnap, cols_max;
+  int R, kfix, khalo;
+  fdtd::cd c1, c2, c3, cs, gs;
+  double C;
+  int64_t rows_done;
+};
 
 // the plan (opaque to users)
 struct fdtd_plan_s {
@@ -120,17 +162,36 @@ struct fdtd_plan_s {
   size_t march_smem;     // dynamic shared memory of the march (delay pair sums)
   int mid_weight;        // column split weight of -a < x <= 3a
   bool record_errors = true;  // false: keep no message (no host allocation on error paths)
+  // complex64 (batched) plans
+  bool batched = false;
+  std::vector<fdtd_batch_inst> inst;
+  size_t off_desc = 0, off_order = 0, off_queue = 0;
+  int csize = 0, nclusters = 0;
+  int64_t smem_cols = 0;
   std::string last_error;
 };
 
 // fills a plan without allocating it (fdtd_plan = new + this)
 fdtd_status fdtd_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n_instances, void* cuda_stream,
                            size_t* workspace_bytes);
+// complex64 (batched) plans: batch_api.cu
+fdtd_status batch_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n, void* cuda_stream,
+                            size_t* workspace_bytes);
+fdtd_status batch_set_boundary(fdtd_plan_s* P, int32_t source, const void* table, int64_t n);
+fdtd_status batch_march(fdtd_plan_s* P, int64_t rows);
+int64_t batch_readout_bytes(fdtd_plan_s* P, int32_t inst, int32_t kind);
+fdtd_status batch_readout(fdtd_plan_s* P, int32_t inst, int32_t kind, void* dst, int64_t dst_bytes);
 
 namespace fdtd {
 // launchers (return cudaError_t)
 cudaError_t launch_boundary(const BoundaryArgs& a, cd* hscratch, bool compute_etable, cudaStream_t s);
 cudaError_t launch_gamma_star(const int32_t* n, const double* z, double* out, int64_t count, cudaStream_t s);
 cudaError_t launch_march_f64(const MarchArgs& a, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_tables32(const InstDesc& I, const cd* detab, const cd* rowscal, cudaStream_t s);
+cudaError_t launch_advance(InstDesc* insts, int ninst, int64_t rows, cudaStream_t s);
+size_t march_f32c_smem(int64_t cols);
+int march_f32c_max_clusters(int csize, size_t smem);
+cudaError_t launch_march_f32c(const InstDesc* insts, const int* order, int ninst, unsigned int* queue,
+                              SyncWords* sync, int nclusters, int csize, size_t smem, cudaStream_t s);
 int march_f64_max_grid(int device);
 }  // namespace fdtd

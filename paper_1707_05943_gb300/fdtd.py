@@ -30,7 +30,7 @@ READ_ROW, READ_NORMS, READ_SNAPSHOTS, READ_ETABLE, READ_ROWS_DONE = range(5)
 
 EXPORTS = ["fdtd_plan", "fdtd_bind_workspace", "fdtd_set_boundary", "fdtd_march", "fdtd_readout",
            "fdtd_readout_bytes", "fdtd_destroy", "fdtd_status_string", "fdtd_last_error", "fdtd_gamma_star",
-           "fdtd_march_noalloc", "fdtd_noalloc_max_bytes"]
+           "fdtd_march_noalloc", "fdtd_noalloc_max_bytes", "fdtd_readout_instance", "fdtd_readout_instance_bytes"]
 
 
 class FdtdParams(ctypes.Structure):
@@ -85,10 +85,13 @@ def lib() -> ctypes.CDLL:
         L.fdtd_last_error.restype = ctypes.c_char_p
         L.fdtd_gamma_star.argtypes = [vp, vp, vp, i64, vp]
         L.fdtd_march_noalloc.argtypes = [ctypes.POINTER(FdtdParams), vp, vp, vp]
+        L.fdtd_readout_instance.argtypes = [vp, i32, i32, vp, i64]
+        L.fdtd_readout_instance_bytes.argtypes = [vp, i32, i32]
+        L.fdtd_readout_instance_bytes.restype = i64
         L.fdtd_noalloc_max_bytes.argtypes = []
         L.fdtd_noalloc_max_bytes.restype = sz
         for f in ("fdtd_plan", "fdtd_bind_workspace", "fdtd_set_boundary", "fdtd_march", "fdtd_readout",
-                  "fdtd_gamma_star", "fdtd_march_noalloc"):
+                  "fdtd_gamma_star", "fdtd_march_noalloc", "fdtd_readout_instance"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -131,6 +134,15 @@ def fdtd_march(plan, n_rows: int):
 
 def fdtd_readout(plan, kind: int, dst_ptr: int, dst_bytes: int):
     _check(lib().fdtd_readout(plan, kind, ctypes.c_void_p(dst_ptr), dst_bytes), plan, "fdtd_readout")
+
+
+def fdtd_readout_instance(plan, instance: int, kind: int, dst_ptr: int, dst_bytes: int):
+    _check(lib().fdtd_readout_instance(plan, instance, kind, ctypes.c_void_p(dst_ptr), dst_bytes), plan,
+           "fdtd_readout_instance")
+
+
+def fdtd_readout_instance_bytes(plan, instance: int, kind: int) -> int:
+    return int(lib().fdtd_readout_instance_bytes(plan, instance, kind))
 
 
 def fdtd_readout_bytes(plan, kind: int) -> int:
