@@ -94,7 +94,7 @@ fdtd_status batch_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n, v
   size_t off = 0;
   P->off_sync = off;  off = align_up(off + sizeof(fdtd::SyncWords));
   P->off_desc = off;  off = align_up(off + sizeof(fdtd::InstDesc) * (size_t)n);
-  P->off_order = off; off = align_up(off + sizeof(int) * (size_t)n);
+  P->off_order = off; off = align_up(off + sizeof(fdtd::WorkItem) * (size_t)n);
   P->off_queue = off; off = align_up(off + sizeof(unsigned int) * 4);
   int64_t cols = 0;
   for (int i = 0; i < n; ++i) {
@@ -139,19 +139,21 @@ fdtd_status batch_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n, v
     b.off_phi32 = off;    off = align_up(off + sizeof(float2) * (size_t)b.nphi);
     b.off_rowscal32 = off; off = align_up(off + 2 * sizeof(float2) * (size_t)p.nt);
     b.off_detab32 = off;  off = align_up(off + sizeof(float2) * (size_t)(p.nt + p.D));
-    b.off_lo = off;       off = align_up(off + sizeof(float2) * (size_t)p.nx);
-    b.off_edge = off;     off = align_up(off + sizeof(float2) * 2 * fdtd::kClusterMax);
+    b.off_lo = off;       off = align_up(off + sizeof(float2) * 2 * (size_t)((p.nx + 4 + 7) / 8 * 8));
+    b.off_bnd = off;      off = align_up(off + sizeof(float2) * 2 * (size_t)p.nt);
+    b.off_bnorm = off;    off = align_up(off + sizeof(double) * (size_t)p.nt);
     b.off_part = off;     off = align_up(off + sizeof(double) * 2 * fdtd::kClusterMax);
     b.off_ring = off;     off = align_up(off + sizeof(float2) * (size_t)b.R * (size_t)b.stride);
     b.off_snaps = off;    off = align_up(off + sizeof(float2) * (size_t)b.nsnap * (size_t)p.nx);
     b.rows_done = 0;
   }
-  P->smem_cols = cols;
-  const size_t smem = fdtd::march_f32c_smem(cols);
-  if (smem + 16 * 1024 > 227 * 1024) return FDTD_ERR_UNSUPPORTED;  // instance too wide for the cluster
+  // pair sums in shared memory when the widest CTA range fits (200 KB); otherwise
+  // the kernel reads both delay rows from L2/HBM
+  P->smem_cols = (fdtd::march_f32c_smem(cols) <= size_t(200) * 1024) ? cols : 0;
+  const size_t smem = fdtd::march_f32c_smem(P->smem_cols);
   int maxc = fdtd::march_f32c_max_clusters(P->csize, smem);
   if (maxc <= 0) return FDTD_ERR_CUDA;
-  P->nclusters = std::min(maxc, n);
+  P->nclusters = maxc;  // capped by the number of work items at set-up
   P->ws_need = off;
   P->state = 0;
   *workspace_bytes = off;
@@ -176,8 +178,8 @@ fdtd_status batch_set_boundary(fdtd_plan_s* P, int32_t source, const void* table
     const fdtd_params& p = b.p;
     e = cudaMemsetAsync(P->ws + b.off_ring, 0, sizeof(float2) * (size_t)b.R * (size_t)b.stride, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->ws + b.off_norms, 0, sizeof(double) * (size_t)p.nt, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(P->ws + b.off_lo, 0, sizeof(float2) * (size_t)p.nx, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(P->ws + b.off_edge, 0, sizeof(float2) * 2 * fdtd::kClusterMax, s);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(P->ws + b.off_lo, 0, sizeof(float2) * 2 * (size_t)((p.nx + 4 + 7) / 8 * 8), s);
     if (e == cudaSuccess && b.nsnap)
       e = cudaMemsetAsync(P->ws + b.off_snaps, 0, sizeof(float2) * (size_t)b.nsnap * (size_t)p.nx, s);
     if (e != cudaSuccess) return cuda_fail(P, e, "cudaMemsetAsync");
@@ -238,8 +240,8 @@ fdtd_status batch_set_boundary(fdtd_plan_s* P, int32_t source, const void* table
     d.delta = p.delta;
     d.ring = at<float2>(P, b.off_ring);
     d.snaps = b.nsnap ? at<float2>(P, b.off_snaps) : nullptr;
-    d.lo_g = at<float2>(P, b.off_lo);
-    d.lo_edge = at<float2>(P, b.off_edge);
+    d.lo = at<float2>(P, b.off_lo);
+    d.lo_pitch = (p.nx + 4 + 7) / 8 * 8;
     d.partials = at<double>(P, b.off_part);
     d.norms = at<double>(P, b.off_norms);
     d.etab = at<cd>(P, b.off_etab);
@@ -248,19 +250,40 @@ fdtd_status batch_set_boundary(fdtd_plan_s* P, int32_t source, const void* table
     d.phitab32 = at<float2>(P, b.off_phi32);
     d.detab32 = at<float2>(P, b.off_detab32);
     d.rowscal32 = at<float2>(P, b.off_rowscal32);
+    d.bnd32 = at<float2>(P, b.off_bnd);
+    d.bnorm = at<double>(P, b.off_bnorm);
     e = fdtd::launch_tables32(d, at<cd>(P, b.off_detab), at<cd>(P, b.off_rowscal), s);
     if (e != cudaSuccess) return cuda_fail(P, e, "tables32");
     b.rows_done = 1;
   }
-  // queue order: largest instances first
+  // work items, largest first: an instance wider than kSoloCols gets the whole
+  // cluster; narrower ones go one per CTA, csize to an item
+  const int64_t kSoloCols = (int64_t)fdtd::kF32Threads * 8;
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
     return P->inst[x].p.nx * P->inst[x].p.nt > P->inst[y].p.nx * P->inst[y].p.nt;
   });
+  std::vector<fdtd::WorkItem> items;
+  for (size_t q = 0; q < order.size();) {
+    fdtd::WorkItem w;
+    memset(&w, 0, sizeof w);
+    if (P->csize == 1 || P->inst[order[q]].p.nx > kSoloCols) {
+      w.count = 1;
+      w.solo = 0;
+      w.inst[0] = order[q++];
+    } else {
+      w.solo = 1;
+      while (w.count < P->csize && q < order.size()) w.inst[w.count++] = order[q++];
+    }
+    items.push_back(w);
+  }
+  P->nitems = (int)items.size();
+  if (P->nclusters > P->nitems) P->nclusters = P->nitems;
   e = cudaMemcpyAsync(P->ws + P->off_desc, desc.data(), sizeof(fdtd::InstDesc) * (size_t)n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(P->ws + P->off_order, order.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(P->ws + P->off_order, items.data(), sizeof(fdtd::WorkItem) * items.size(),
+                        cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(P, e, "cudaMemcpyAsync(descriptors)");
   // the pageable copies above are staged before they return
   P->rows_done = 1;
@@ -282,7 +305,7 @@ fdtd_status batch_march(fdtd_plan_s* P, int64_t rows) {
     cudaError_t e = fdtd::launch_advance(at<fdtd::InstDesc>(P, P->off_desc), n, step, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->ws + P->off_queue, 0, sizeof(unsigned int), s);
     if (e == cudaSuccess)
-      e = fdtd::launch_march_f32c(at<fdtd::InstDesc>(P, P->off_desc), at<int>(P, P->off_order), n,
+      e = fdtd::launch_march_f32c(at<fdtd::InstDesc>(P, P->off_desc), at<fdtd::WorkItem>(P, P->off_order), P->nitems,
                                   at<unsigned int>(P, P->off_queue), at<fdtd::SyncWords>(P, P->off_sync),
                                   P->nclusters, P->csize, smem, s);
     if (e != cudaSuccess) return cuda_fail(P, e, "march_f32c launch");

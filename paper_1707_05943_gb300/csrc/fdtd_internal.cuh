@@ -42,7 +42,7 @@ constexpr int kMaxTrunc = 64;        // cap on scan / halo truncation depth
 constexpr int kMaxGrid = 1024;       // cap on CTAs of the persistent march
 
 // complex64 compensated march (march_f32c.cu)
-constexpr int kF32Threads = 512;     // threads per CTA
+constexpr int kF32Threads = 256;     // threads per CTA
 constexpr int kF32P = 8;             // leading columns of a segment kept in registers
 constexpr int kF32MaxTrunc = 16;     // |c2|^16 < 2^-26 required (|c2| < 0.32)
 constexpr int kClusterMax = 16;      // CTAs per cluster at most
@@ -106,15 +106,15 @@ struct BoundaryArgs {
 struct InstDesc {
   int64_t nx, nt, stride, nphi;
   int64_t range[2];        // rows [range[0], range[1]) marched by the current launch; range[1] = rows done
-  int64_t smem_cols;       // shared-memory columns per CTA available to the launch
+  int64_t smem_cols;       // pair-sum columns per CTA that fit the launch's shared memory
   int D, R, kfix, khalo, mid_weight, tstep;
   float2 d1, c2, c3, gs;   // c1 - 1, c2, c3, -(Gamma/4)/A
   float2 c2pow[kF32MaxTrunc + 1];
   double C, delta;
   float2* ring;            // R rows x stride complex64
   float2* snaps;           // or null
-  float2* lo_g;            // nx: a_lo carried between launches
-  float2* lo_edge;         // 2 x kClusterMax: a_lo at CTA edges
+  float2* lo;              // 2 x lo_pitch: TwoSum remainders by consumer column, two row slots
+  int64_t lo_pitch;        // >= nx + 4, a multiple of 8 elements (slots 64-byte aligned)
   double* partials;        // 2 x kClusterMax
   double* norms;           // nt
   const cd* etab;          // FP64 tables
@@ -123,6 +123,15 @@ struct InstDesc {
   const float2* phitab32;
   const float2* detab32;
   const float2* rowscal32;
+  const float2* bnd32;     // 2 per row: psi(-a, n delta) as FP32 hi and lo
+  const double* bnorm;     // per row: (1/2)|psi(-a, n delta)|^2
+};
+
+// one entry of the batched march's queue
+struct WorkItem {
+  int count;               // instances in the item
+  int solo;                // 1: one instance per CTA; 0: inst[0] over the whole cluster
+  int inst[kClusterMax];
 };
 
 }  // namespace fdtd
@@ -131,7 +140,7 @@ struct InstDesc {
 struct fdtd_batch_inst {
   fdtd_params p;
   size_t off_etab, off_phi, off_rowscal, off_detab, off_norms, off_hscr, off_etab32, off_phi32, off_rowscal32,
-      off_detab32, off_ring, off_snaps, off_lo, off_edge, off_part;
+      off_detab32, off_ring, off_snaps, off_lo, off_part, off_bnd, off_bnorm;
   int64_t stride, nphi, nsnap, cols_max;
   int R, kfix, khalo;
   fdtd::cd c1, c2, c3, cs, gs;
@@ -166,6 +175,7 @@ struct fdtd_plan_s {
   bool batched = false;
   std::vector<fdtd_batch_inst> inst;
   size_t off_desc = 0, off_order = 0, off_queue = 0;
+  int nitems = 0;
   int csize = 0, nclusters = 0;
   int64_t smem_cols = 0;
   std::string last_error;
@@ -191,7 +201,7 @@ cudaError_t launch_tables32(const InstDesc& I, const cd* detab, const cd* rowsca
 cudaError_t launch_advance(InstDesc* insts, int ninst, int64_t rows, cudaStream_t s);
 size_t march_f32c_smem(int64_t cols);
 int march_f32c_max_clusters(int csize, size_t smem);
-cudaError_t launch_march_f32c(const InstDesc* insts, const int* order, int ninst, unsigned int* queue,
+cudaError_t launch_march_f32c(const InstDesc* insts, const WorkItem* items, int nitems, unsigned int* queue,
                               SyncWords* sync, int nclusters, int csize, size_t smem, cudaStream_t s);
 int march_f64_max_grid(int device);
 }  // namespace fdtd

@@ -9,15 +9,16 @@
 // along its characteristic as an unevaluated pair a_hi + a_lo: a_hi is the
 // complex64 value in the ring, a_lo the rounding error of the sum that
 // produced it, recovered exactly by TwoSum(a_hi, S) (Knuth) and kept on chip
-// (shared memory, the CTA edge in a two-slot global array) until the next row
-// consumes it at column m+1.  The boundary tables, the exact boundary value
+// (a two-slot array by row parity, L2-resident) until the next row consumes it
+// at column m+1.  The boundary tables, the exact boundary value
 // psi(-a, t) at the first column and the norm reduction stay FP64.
 //
 // Work layout: thread-block clusters of up to 16 CTAs x 512 threads.  A
-// cluster takes the next instance from a queue (largest first), splits its
-// columns over its CTAs (weighting the costlier region -a < x <= 3a), and
-// marches the instance's rows with one cluster barrier per row; rows n-1, n-D
-// and n-D-1 are then complete.  Inside a CTA each thread owns a contiguous
+// cluster takes the next work item from a queue (largest first): either one
+// wide instance, whose columns it splits over its CTAs (weighting the costlier
+// region -a < x <= 3a) and whose rows it marches with one cluster barrier per
+// row, or up to one narrow instance per CTA, marched with CTA barriers only.
+// Either way rows n-1, n-D and n-D-1 are complete when row n starts.  Inside a CTA each thread owns a contiguous
 // segment and runs the recurrence y_m = c2 y_{m-1} + r_m over it from a zero
 // carry; after a CTA barrier it takes its carry from the threads before it
 // and corrects its first kfix columns (|c2|^kfix < 2^-26, below FP32
@@ -76,36 +77,60 @@ struct RowF {
   bool cold;
 };
 
-// S without the a_lo and c2 y_{m-1} parts, and a_hi, for a column of -a < x <= 3a
+// S without the a_lo and c2 y_{m-1} parts, and a_hi, for a column of -a < x <= 3a.
+// Its up to 14 reads (stencil, delay square, the mirror bars of lines 2-3) go
+// to scattered rows; they are all issued before any is used.
 __device__ __noinline__ float2 rhs_general32(const InstDesc& I, int64_t n, int nslot, int64_t j, float2 R2,
                                              float2* a_hi) {
   const int D = I.D, Dh = D >> 1;
   const int64_t m = j - Dh + 1;
-  float2 a = psi_any32(I, n, nslot, n - 1, m - 1);
-  *a_hi = a;
-  float2 S = mulc(I.d1, a);
-  S = fmac(I.c2, psi_any32(I, n, nslot, n - 1, m), S);
-  if (n >= D + 1) {
-    float2 sq = add(add(psi_any32(I, n, nslot, n - D, m - D), psi_any32(I, n, nslot, n - D, m - D - 1)),
-                    add(psi_any32(I, n, nslot, n - D - 1, m - D), psi_any32(I, n, nslot, n - D - 1, m - D - 1)));
-    S = fmac(I.c3, sq, S);
+  const int64_t r2 = n - m - Dh, r3 = n - m + Dh;
+  const bool dl = (n >= D + 1), s2 = (r2 >= 0), s3 = (m >= Dh + 1) && (r3 >= 0);
+  int64_t rr[14], cc[14];
+  bool ok[14];
+  rr[0] = n - 1; cc[0] = m - 1; ok[0] = true;
+  rr[1] = n - 1; cc[1] = m; ok[1] = true;
+  rr[2] = n - D; cc[2] = m - D; rr[3] = n - D; cc[3] = m - D - 1;
+  rr[4] = n - D - 1; cc[4] = m - D; rr[5] = n - D - 1; cc[5] = m - D - 1;
+  ok[2] = ok[3] = ok[4] = ok[5] = dl;
+  rr[6] = r2; cc[6] = -m - D; rr[7] = r2; cc[7] = -m - D + 1; rr[8] = r2; cc[8] = -m; rr[9] = r2; cc[9] = -m + 1;
+  ok[6] = ok[7] = ok[8] = ok[9] = s2;
+  rr[10] = r3; cc[10] = D - m; rr[11] = r3; cc[11] = D - m + 1; rr[12] = r3; cc[12] = -m; rr[13] = r3; cc[13] = -m + 1;
+  ok[10] = ok[11] = ok[12] = ok[13] = s3;
+  // unconditional loads (indices clamped into the tables and the ring), selected below
+  float2 ph[14], ev[14], rg[14];
+#pragma unroll
+  for (int k = 0; k < 14; ++k) {
+    int64_t ai = rr[k] - cc[k] - Dh;
+    ai = ai < 0 ? 0 : (ai >= I.nphi ? I.nphi - 1 : ai);
+    int64_t ei = rr[k] < 0 ? 0 : (rr[k] >= I.nt ? I.nt - 1 : rr[k]);
+    int lag = (int)(n - rr[k]);
+    lag = lag < 0 ? 0 : (lag >= I.R ? I.R - 1 : lag);
+    int slot = nslot - lag;
+    if (slot < 0) slot += I.R;
+    int64_t ci = cc[k] + Dh - 1;
+    ci = ci < 0 ? 0 : (ci >= I.nx ? I.nx - 1 : ci);
+    ph[k] = I.phitab32[ai];
+    ev[k] = I.etab32[ei];
+    rg[k] = ldr(&I.ring[(int64_t)slot * I.stride + ci]);
   }
-  const int64_t r2 = n - m - Dh;
-  if (r2 >= 0) {
-    float w = (r2 == 0) ? 0.5f : 1.0f;
-    float2 bl = add(psi_any32(I, n, nslot, r2, -m - D), psi_any32(I, n, nslot, r2, -m - D + 1));
-    float2 br = add(psi_any32(I, n, nslot, r2, -m), psi_any32(I, n, nslot, r2, -m + 1));
-    S = fmac(I.gs, scal(w, sub(bl, br)), S);
-    S = fmac(R2, I.phitab32[r2], S);
+  const float2 chi = I.phitab32[s2 ? r2 : 0];
+  float2 v[14];
+#pragma unroll
+  for (int k = 0; k < 14; ++k)
+    v[k] = !ok[k] ? f2(0.f, 0.f) : ((cc[k] <= -Dh) ? scal((float)I.C, mulc(ph[k], ev[k])) : rg[k]);
+  *a_hi = v[0];
+  float2 S = mulc(I.d1, v[0]);
+  S = fmac(I.c2, v[1], S);
+  if (dl) S = fmac(I.c3, add(add(v[2], v[3]), add(v[4], v[5])), S);
+  if (s2) {
+    const float w = (r2 == 0) ? 0.5f : 1.0f;
+    S = fmac(I.gs, scal(w, sub(add(v[6], v[7]), add(v[8], v[9]))), S);
+    S = fmac(R2, chi, S);
   }
-  if (m >= Dh + 1) {
-    const int64_t r3 = n - m + Dh;
-    if (r3 >= 0) {
-      float w = (r3 == 0) ? 0.5f : 1.0f;
-      float2 bl = add(psi_any32(I, n, nslot, r3, D - m), psi_any32(I, n, nslot, r3, D - m + 1));
-      float2 br = add(psi_any32(I, n, nslot, r3, -m), psi_any32(I, n, nslot, r3, -m + 1));
-      S = fmac(I.gs, scal(w, sub(bl, br)), S);
-    }
+  if (s3) {
+    const float w = (r3 == 0) ? 0.5f : 1.0f;
+    S = fmac(I.gs, scal(w, sub(add(v[10], v[11]), add(v[12], v[13]))), S);
   }
   return S;
 }
@@ -160,6 +185,14 @@ __device__ __forceinline__ int ld_dsmem_i32(const int* local, unsigned rank) {
   return v;
 }
 
+__device__ __forceinline__ float ld_dsmem_f32(const float* local, unsigned rank) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(local), ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(ra) : "r"(a), "r"(rank));
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];\n" : "=f"(v) : "r"(ra) : "memory");
+  return v;
+}
+
 // columns of CTA `rank` of `C` for an instance: split by cost
 __device__ __forceinline__ void cta_range(const InstDesc& I, int rank, int C, int64_t* lo, int64_t* hi) {
   const int64_t G2 = (2 * (int64_t)I.D < I.nx) ? 2 * (int64_t)I.D : I.nx;
@@ -170,248 +203,394 @@ __device__ __forceinline__ void cta_range(const InstDesc& I, int rank, int C, in
   *hi = inv(W * (rank + 1) / C);
 }
 
+// ---- TMA bulk copies into shared memory (1D), completion on an mbarrier ----
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(bar), ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// copy `bytes` (multiple of 16) from 16-byte aligned global memory to shared memory
+__device__ __forceinline__ void tma_load_1d(void* sdst, const void* gsrc, unsigned bytes, uint64_t* bar) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(sdst), m = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(d),
+               "l"(gsrc), "r"(bytes), "r"(m)
+               : "memory");
+}
+
+// A staged slice: global elements [g0, g1) of a float2 array start at smem
+// element `off` (0 or 1: the copy starts on an even element, 16-byte aligned).
+struct Slice {
+  float2* s;
+  int off;
+  int64_t g0;
+  __device__ __forceinline__ float2 at(int64_t g) const { return s[g - g0 + off]; }
+};
+
+// plan the copy of global elements [g0, g1) into `dst`: the copy starts on an
+// even element (16-byte aligned) and moves an even number of elements
+struct Copy {
+  float2* dst;
+  const float2* src;
+  unsigned bytes;
+};
+__device__ __forceinline__ Copy plan_copy(Slice& sl, float2* dst, const float2* src, int64_t g0, int64_t g1) {
+  const int64_t a = g0 & ~int64_t(1), b = (g1 + 1) & ~int64_t(1);
+  sl.s = dst;
+  sl.off = (int)(g0 - a);
+  sl.g0 = g0;
+  return Copy{dst, src + a, (unsigned)((b - a) * sizeof(float2))};
+}
+
+constexpr int kBlk = 2048;        // bulk columns staged per block
+constexpr int kStageCols = kBlk + 4;
+
 __global__ void __launch_bounds__(kF32Threads, 1)
-    k_march_f32c(const InstDesc* __restrict__ insts, const int* __restrict__ order, int ninst,
+    k_march_f32c(const InstDesc* __restrict__ insts, const WorkItem* __restrict__ items, int nitems,
                  unsigned int* queue, SyncWords* sync) {
-  constexpr int P = kF32P;
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(128) float2 smem[];
   __shared__ float2 s_last[kF32Threads];
   __shared__ int s_len[kF32Threads];
   __shared__ float2 s_carry;
   __shared__ float2 s_halo[kMaxTrunc];
-  __shared__ double s_red[kF32Threads / 32];
+  __shared__ float s_red[2][kF32Threads / 32];
   __shared__ int s_inst;
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ __align__(16) InstDesc s_I;  // the instance's descriptor: no global store can alias it
 
   const int tid = threadIdx.x;
   const unsigned rank = cluster_rank(), C = cluster_size();
+  // shared memory: 6 staging slices, then the pair sums of the CTA's columns
+  float2* st_a1 = smem;
+  float2* st_ad = st_a1 + kStageCols;
+  float2* st_ad1 = st_ad + kStageCols;
+  float2* st_lo = st_ad1 + kStageCols;
+  float2* st_de = st_lo + kStageCols;
+  float2* st_ph = st_de + kStageCols;
+  float2* o_hi = st_ph + kStageCols;  // block results: hi (or parked S), remainder (or parked a_hi)
+  float2* o_e = o_hi + kStageCols;
+  float2* hs_base = o_e + kStageCols;
+  if (tid == 0) mbar_init(&s_bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  __syncthreads();
+  unsigned bar_phase = 0;
 
   for (;;) {
-    // the cluster's next instance
+    // the cluster's next work item: one wide instance for the whole cluster, or
+    // up to C narrow instances, one per CTA ("solo": CTA barriers only)
     if (rank == 0 && tid == 0) {
       unsigned q = atomicAdd(queue, 1u);
-      s_inst = (q < (unsigned)ninst) ? order[q] : -1;
+      s_inst = (q < (unsigned)nitems) ? (int)q : -1;
     }
     cluster_sync_all();
-    const int inst = ld_dsmem_i32(&s_inst, 0);
+    const int item = ld_dsmem_i32(&s_inst, 0);
     cluster_sync_all();  // s_inst is read by every CTA before rank 0 may overwrite it
-    if (inst < 0) break;
-    const InstDesc& I = insts[inst];
-    const int64_t n_begin = I.range[0], n_end = I.range[1];
-    if (n_begin >= n_end) continue;
-    const int D = I.D;
-
-    int64_t j_lo, j_hi;
-    cta_range(I, (int)rank, (int)C, &j_lo, &j_hi);
-    const int64_t L = j_hi - j_lo;
-    const int64_t G2 = (2 * (int64_t)D < I.nx) ? 2 * (int64_t)D : I.nx;
-    int64_t s0, s1;
-    if (j_lo >= G2) {
-      const int64_t seg = ((L + kF32Threads - 1) / kF32Threads) | 1;
-      s0 = j_lo + (int64_t)tid * seg;
-      if (s0 > j_hi) s0 = j_hi;
-      s1 = (s0 + seg < j_hi) ? s0 + seg : j_hi;
-    } else {
-      const int64_t wm = I.mid_weight;
-      auto cumw = [&](int64_t j) { return j <= G2 ? wm * j : wm * G2 + (j - G2); };
-      auto inv = [&](int64_t x) { return x <= wm * G2 ? (x + wm - 1) / wm : G2 + (x - wm * G2); };
-      const int64_t W0 = cumw(j_lo), W1 = cumw(j_hi);
-      s0 = inv(W0 + (W1 - W0) * tid / kF32Threads);
-      s1 = inv(W0 + (W1 - W0) * (tid + 1) / kF32Threads);
-    }
-    const int64_t h0 = (j_lo - I.khalo > 0) ? j_lo - I.khalo : 0;
-    const int nh = (int)(j_lo - h0);
-    // shared memory: pair sums (khalo + L), then two slots of a_lo (L + 1 each)
-    const int64_t hcap = I.smem_cols;
-    float2* hs = smem;
-    float2* es0 = smem + hcap;
-    float2* es1 = es0 + (hcap + 1);
-    const bool reuse = (L + nh <= hcap);
-    s_len[tid] = (int)(s1 - s0);
-    // a_lo of row n_begin-1, saved by the previous launch
-    {
-      float2* es = ((n_begin - 1) & 1) ? es1 : es0;
-      for (int64_t j = j_lo + tid; j <= j_hi && reuse; j += kF32Threads)
-        es[j - j_lo] = (j < I.nx && j - 1 >= 0) ? I.lo_g[j - 1] : f2(0.f, 0.f);
+    if (item < 0) break;
+    const WorkItem& Wk = items[item];
+    const bool solo = Wk.solo != 0;
+    const int inst = solo ? ((rank < (unsigned)Wk.count) ? Wk.inst[rank] : -1) : Wk.inst[0];
+    const unsigned rank_e = solo ? 0u : rank, C_e = solo ? 1u : C;
+    if (inst >= 0) {
+      const int* src = reinterpret_cast<const int*>(&insts[inst]);
+      int* dst = reinterpret_cast<int*>(&s_I);
+      for (int k = tid; k < (int)(sizeof(InstDesc) / sizeof(int)); k += kF32Threads) dst[k] = src[k];
     }
     __syncthreads();
+    if (inst >= 0 && s_I.range[0] < s_I.range[1]) {
+      const InstDesc& I = s_I;
+      const int64_t n_begin = I.range[0], n_end = I.range[1];
+      const int D = I.D;
+      int64_t j_lo, j_hi;
+      cta_range(I, (int)rank_e, (int)C_e, &j_lo, &j_hi);
+      const int64_t G2 = (2 * (int64_t)D < I.nx) ? 2 * (int64_t)D : I.nx;
+      const int64_t h0 = (j_lo - I.khalo > 0) ? j_lo - I.khalo : 0;
+      const int nh = (int)(j_lo - h0);
+      const bool reuse = (j_hi - j_lo + nh <= I.smem_cols);  // pair sums kept in shared memory
+      float2* hs = reuse ? hs_base : nullptr;
 
-    for (int64_t n = n_begin; n < n_end; ++n) {
-      RowF R;
-      R.n = n;
-      R.nslot = (int)(n % I.R);
-      R.row1 = I.ring + (int64_t)((n - 1) % I.R) * I.stride;
-      R.rowD = (n >= D) ? I.ring + (int64_t)((n - D) % I.R) * I.stride : nullptr;
-      R.rowD1 = (n >= D + 1) ? I.ring + (int64_t)((n - D - 1) % I.R) * I.stride : nullptr;
-      float2* row0 = I.ring + (int64_t)R.nslot * I.stride;
-      float2* snap =
-          (I.snaps && I.tstep >= 0 && n % (I.tstep + 1) == 0) ? I.snaps + (n / (I.tstep + 1)) * I.nx : nullptr;
-      R.R1 = I.rowscal32[2 * n];
-      R.R2 = I.rowscal32[2 * n + 1];
-      R.hs = reuse ? hs : nullptr;
-      R.hbase = h0;
-      R.cold = (n == n_begin);
-      float2* es_rd = ((n - 1) & 1) ? es1 : es0;  // a_lo of row n-1, by consumer column
-      float2* es_wr = (n & 1) ? es1 : es0;        // a_lo for row n+1
+      int slot = (int)(n_begin % I.R);
+      int64_t snap_ctr = (I.tstep >= 0) ? n_begin % (I.tstep + 1) : -1;
+      for (int64_t n = n_begin; n < n_end; ++n) {
+        auto back = [&](int k) { int t = slot - k; return t < 0 ? t + I.R : t; };
+        RowF R;
+        R.n = n;
+        R.nslot = slot;
+        R.row1 = I.ring + (int64_t)back(1) * I.stride;
+        R.rowD = (n >= D) ? I.ring + (int64_t)back(D) * I.stride : nullptr;
+        R.rowD1 = (n >= D + 1) ? I.ring + (int64_t)back(D + 1) * I.stride : nullptr;
+        float2* row0 = I.ring + (int64_t)slot * I.stride;
+        float2* snap = (snap_ctr == 0) ? I.snaps + (n / (I.tstep + 1)) * I.nx : nullptr;
+        R.R1 = I.rowscal32[2 * n];
+        R.R2 = I.rowscal32[2 * n + 1];
+        R.hs = hs;
+        R.hbase = h0;
+        R.cold = (n == n_begin);
+        float2* es_rd = I.lo + (int64_t)((n - 1) & 1) * I.lo_pitch;
+        float2* es_wr = I.lo + (int64_t)(n & 1) * I.lo_pitch;
+        float nacc = 0.f;
 
-      if (tid < 32 && j_lo < j_hi) {
-        // the CTA's first column: the exact boundary value (first CTA) or the left CTA's edge
-        if (tid == 0) {
-          if (j_lo == 0) {
-            const cd ex = I.C * (I.phitab[n - 1] * I.etab[n - 1]);  // psi(-a, (n-1) delta), FP64
-            es_rd[0] = f2((float)(ex.re - (double)(float)ex.re), (float)(ex.im - (double)(float)ex.im));
-          } else {
-            es_rd[0] = I.lo_edge[((n - 1) & 1) * kClusterMax + rank - 1];
+        // carry into the CTA's first column: psi(-a) for the first CTA, else the
+        // recurrence over khalo columns to its left (warp 0)
+        if (tid < 32 && j_lo < j_hi) {
+          if (tid == 0 && j_lo == 0) es_rd[0] = I.bnd32[2 * (n - 1) + 1];  // thread 0 owns column 0
+          for (int c = tid; c < nh; c += 32) {
+            float2 ah;
+            float2 S = rhs32(I, R, h0 + c, &ah);
+            s_halo[c] = add(ah, S);
+          }
+          __syncwarp();
+          if (tid == 0) {
+            float2 yh = (h0 == 0) ? I.bnd32[2 * n] : f2(0.f, 0.f);
+            for (int c = 0; c < nh; ++c) yh = fmac(I.c2, yh, s_halo[c]);
+            s_carry = yh;
           }
         }
-        for (int c = tid; c < nh; c += 32) {
-          float2 ah;
-          float2 S = rhs32(I, R, h0 + c, &ah);
-          s_halo[c] = add(ah, S);
-        }
-        __syncwarp();
-        if (tid == 0) {
+
+        // blocks: first the columns of -a < x <= 3a (read in place, cost-weighted
+        // over the threads), then x > 3a in staged blocks of kBlk
+        int64_t c0 = j_lo;
+        while (c0 < j_hi) {
+          const bool gen = (c0 < G2);
+          const int64_t c1 = gen ? ((j_hi < G2) ? j_hi : G2) : ((c0 + kBlk < j_hi) ? c0 + kBlk : j_hi);
+          const int64_t len = c1 - c0;
+          // this thread's segment of the block
+          int64_t t0, t1;
+          if (!gen) {
+            const int64_t seg = ((len + kF32Threads - 1) / kF32Threads) | 1;
+            t0 = c0 + (int64_t)tid * seg;
+            if (t0 > c1) t0 = c1;
+            t1 = (t0 + seg < c1) ? t0 + seg : c1;
+          } else {
+            t0 = c0 + len * tid / kF32Threads;
+            t1 = c0 + len * (tid + 1) / kF32Threads;
+          }
+          s_len[tid] = (int)(t1 - t0);
+
+          Slice A1, AD, AD1, LO, DE, PH;
+          const int64_t ib = n - c1 + D;  // detab index of the block's last column
+          if (!gen) {
+            // stage the block's inputs: every thread plans the same six slices;
+            // thread 0 arms the barrier with their bytes and issues the copies
+            const int64_t ilo = (ib > 0) ? ib : 0, ihi = n - c0 + D;        // detab [ilo, ihi)
+            const int64_t plo = (ib - D > 0) ? ib - D : 0, phi_ = n - c0;  // phitab [plo, phi_)
+            Copy cp[6];
+            cp[0] = plan_copy(A1, st_a1, R.row1, c0 - 1, c1);
+            cp[1] = R.rowD ? plan_copy(AD, st_ad, R.rowD, c0 - D - 1, c1 - D) : Copy{nullptr, nullptr, 0u};
+            cp[2] = (R.rowD1 && (!hs || R.cold)) ? plan_copy(AD1, st_ad1, R.rowD1, c0 - D - 1, c1 - D)
+                                                 : Copy{nullptr, nullptr, 0u};
+            cp[3] = plan_copy(LO, st_lo, es_rd, c0, c1);
+            cp[4] = (ihi > ilo) ? plan_copy(DE, st_de, I.detab32, ilo, ihi) : Copy{nullptr, nullptr, 0u};
+            cp[5] = (phi_ > plo) ? plan_copy(PH, st_ph, I.phitab32, plo, phi_) : Copy{nullptr, nullptr, 0u};
+            if (tid == 0) {
+              unsigned bytes = 0;
+              for (int k = 0; k < 6; ++k) bytes += cp[k].bytes;
+              asm volatile("fence.proxy.async;\n" ::: "memory");
+              mbar_expect_tx(&s_bar, bytes);
+              for (int k = 0; k < 6; ++k)
+                if (cp[k].bytes) tma_load_1d(cp[k].dst, cp[k].src, cp[k].bytes, &s_bar);
+            }
+            // bounded wait for the copies
+            long long tw = clock64();
+            while (!mbar_try_wait(&s_bar, bar_phase)) {
+              if (clock64() - tw > 4000000000LL) {
+                if (atomicCAS(&sync->status, 0u, (unsigned)FDTD_ERR_TIMEOUT) == 0u) sync->where = n;
+                break;
+              }
+            }
+            bar_phase ^= 1u;
+          }
+
+          // pass A: the segment from a zero carry; its first kfix columns are
+          // parked (S, a_hi) until pass B adds the carry.  Results of a staged
+          // block go to shared memory (o_hi: hi or parked S, o_e: remainder or
+          // parked a_hi) and leave in coalesced stores after pass B; a block of
+          // -a < x <= 3a writes its few columns in place.
           float2 y = f2(0.f, 0.f);
-          if (h0 == 0) {
-            const cd ex = I.C * (I.phitab[n] * I.etab[n]);  // psi(-a, n delta)
-            y = f2((float)ex.re, (float)ex.im);
-          }
-          for (int c = 0; c < nh; ++c) y = fmac(I.c2, y, s_halo[c]);
-          s_carry = y;
-        }
-      }
-      __syncthreads();  // es_rd[0] and s_carry ready
-
-      // pass A
-      float2 ahv[P], Sv[P];
-      float2 y = f2(0.f, 0.f);
-      float nacc = 0.f;
-#pragma unroll
-      for (int v = 0; v < P; ++v) {
-        const int64_t j = s0 + v;
-        ahv[v] = f2(0.f, 0.f);
-        Sv[v] = f2(0.f, 0.f);
-        if (j < s1) {
-          float2 ah;
-          float2 S = rhs32(I, R, j, &ah);
-          if (j == 0) ah = f2((float)(I.C * (I.phitab[n - 1] * I.etab[n - 1]).re),
-                              (float)(I.C * (I.phitab[n - 1] * I.etab[n - 1]).im));
-          S = add(S, es_rd[j - j_lo]);
-          S = fmac(I.c2, y, S);
-          ahv[v] = ah;
-          Sv[v] = S;
-          y = add(ah, S);
-        }
-      }
-      for (int64_t j = s0 + P; j < s1; ++j) {
-        float2 ah;
-        float2 S = rhs32(I, R, j, &ah);
-        S = add(S, es_rd[j - j_lo]);
-        S = fmac(I.c2, y, S);
-        if (j - s0 < I.kfix) {
-          // still receives the carry: park S and a_hi in the slots this thread fills in pass B
-          row0[j] = S;
-          es_wr[j + 1 - j_lo] = ah;
-          y = add(ah, S);
-        } else {
-          float2 s, e;
-          two_sum(ah.x, S.x, s.x, e.x);
-          two_sum(ah.y, S.y, s.y, e.y);
-          row0[j] = s;
-          if (snap) snap[j] = s;
-          es_wr[j + 1 - j_lo] = e;
-          nacc = fmaf(s.x, s.x, nacc);
-          nacc = fmaf(s.y, s.y, nacc);
-          y = s;
-        }
-      }
-      s_last[tid] = (s0 < s1) ? y : f2(0.f, 0.f);
-      __syncthreads();
-
-      // pass B: carry, correction of the first kfix columns, TwoSum
-      if (s0 < s1) {
-        float2 carry = f2(0.f, 0.f), ap = f2(1.f, 0.f);
-        for (int s = 1; s <= tid + 1; ++s) {
-          if (tid - s >= 0) {
-            carry = fmac(ap, s_last[tid - s], carry);
-            const int lu = s_len[tid - s];
-            ap = mulc(ap, (lu <= kF32MaxTrunc) ? I.c2pow[lu] : f2(0.f, 0.f));
-            if (ap.x * ap.x + ap.y * ap.y < 2.2e-16f) break;  // (2^-26)^2
+          int v = 0;
+          float2* oh = gen ? row0 + c0 : o_hi;      // column j at oh[j - c0]
+          float2* oe = gen ? es_wr + c0 + 1 : o_e;  // remainder of column j at oe[j - c0]
+          auto emit = [&](int64_t j, float2 ah, float2 S) {
+            if (v < I.kfix) {
+              oh[j - c0] = S;
+              oe[j - c0] = ah;
+              y = add(ah, S);
+            } else {
+              float2 sv, e;
+              two_sum(ah.x, S.x, sv.x, e.x);
+              two_sum(ah.y, S.y, sv.y, e.y);
+              oh[j - c0] = sv;
+              oe[j - c0] = e;
+              const float wt = (j == I.nx - 1) ? 0.5f : 1.0f;
+              nacc = fmaf(wt * sv.x, sv.x, nacc);
+              nacc = fmaf(wt * sv.y, sv.y, nacc);
+              y = sv;
+            }
+            ++v;
+          };
+          if (gen) {
+            for (int64_t j = t0; j < t1; ++j) {
+              float2 ah;
+              float2 S = rhs_general32(I, n, R.nslot, j, R.R2, &ah);
+              if (j == 0) ah = I.bnd32[2 * (n - 1)];
+              S = add(S, __ldcg(es_rd + j));
+              emit(j, ah, fmac(I.c2, y, S));
+            }
           } else {
-            carry = fmac(ap, s_carry, carry);
+            // block-relative 32-bit offsets: column j = c0 + k
+            const bool d1 = (R.rowD1 != nullptr), dd = (R.rowD != nullptr);
+            const bool use_hs = hs && !R.cold;
+            const float2* a1s = A1.s + A1.off;                 // a_hi(k) = a1s[k], b(k) = a1s[k+1]
+            const float2* ads = AD.s + AD.off;                 // row n-D: ads[k], ads[k+1]
+            const float2* ad1s = AD1.s + AD1.off;
+            const float2* los = LO.s + LO.off;
+            const int kde = (int)(n - c0 - 1 + D);             // i(k) = kde - k
+            const float2* des = DE.s + DE.off - DE.g0;         // detab32[i] = des[i]
+            const float2* phs = PH.s + PH.off - PH.g0;         // phitab32[i - D] = phs[i - D]
+            float2* hsb = hs ? hs + (c0 - h0) : nullptr;
+            const int k0 = (int)(t0 - c0), k1 = (int)(t1 - c0);
+            const int klast = (int)(I.nx - 1 - c0);
+            const float2 d1c = I.d1, c2c = I.c2, c3c = I.c3, R1 = R.R1, R2 = R.R2;
+            const int kfix = I.kfix;
+            for (int k = k0; k < k1; ++k) {
+              const float2 a = a1s[k], b = a1s[k + 1];
+              float2 S = mulc(d1c, a);
+              S = fmac(c2c, b, S);
+              if (dd) {
+                const float2 hn = add(ads[k], ads[k + 1]);
+                if (d1) S = fmac(c3c, add(hn, use_hs ? hsb[k] : add(ad1s[k], ad1s[k + 1])), S);
+                if (hsb) hsb[k] = hn;
+              }
+              const int i = kde - k;
+              if (i >= 0) S = fmac(R1, des[i], S);
+              if (i >= D) S = fmac(R2, phs[i - D], S);
+              S = add(S, los[k]);
+              S = fmac(c2c, y, S);
+              if (v < kfix) {
+                o_hi[k] = S;
+                o_e[k] = a;
+                y = add(a, S);
+              } else {
+                float2 sv, e;
+                two_sum(a.x, S.x, sv.x, e.x);
+                two_sum(a.y, S.y, sv.y, e.y);
+                o_hi[k] = sv;
+                o_e[k] = e;
+                const float wt = (k == klast) ? 0.5f : 1.0f;
+                nacc = fmaf(wt * sv.x, sv.x, nacc);
+                nacc = fmaf(wt * sv.y, sv.y, nacc);
+                y = sv;
+              }
+              ++v;
+            }
           }
-        }
-#pragma unroll
-        for (int v = 0; v < P; ++v) {
-          const int64_t j = s0 + v;
-          if (j < s1) {
-            float2 S = (v < I.kfix) ? fmac(I.c2pow[v + 1], carry, Sv[v]) : Sv[v];
-            float2 s, e;
-            two_sum(ahv[v].x, S.x, s.x, e.x);
-            two_sum(ahv[v].y, S.y, s.y, e.y);
-            row0[j] = s;
-            if (snap) snap[j] = s;
-            es_wr[j + 1 - j_lo] = e;
-            nacc = fmaf(s.x, s.x, nacc);
-            nacc = fmaf(s.y, s.y, nacc);
-          }
-        }
-        for (int v = P; v < I.kfix && s0 + v < s1; ++v) {
-          const int64_t j = s0 + v;
-          const float2 S = fmac(I.c2pow[v + 1], carry, row0[j]);
-          const float2 ah = es_wr[j + 1 - j_lo];
-          float2 s, e;
-          two_sum(ah.x, S.x, s.x, e.x);
-          two_sum(ah.y, S.y, s.y, e.y);
-          row0[j] = s;
-          if (snap) snap[j] = s;
-          es_wr[j + 1 - j_lo] = e;
-          nacc = fmaf(s.x, s.x, nacc);
-          nacc = fmaf(s.y, s.y, nacc);
-        }
-        if (s1 == j_hi) {  // the CTA's last column: its a_lo goes to the next CTA
-          I.lo_edge[(n & 1) * kClusterMax + rank] = es_wr[j_hi - j_lo];
-        }
-      }
+          s_last[tid] = (t0 < t1) ? y : f2(0.f, 0.f);
+          __syncthreads();
 
-      // norm partial: FP32 within a thread (its few columns), FP64 from there on
-      double dn = (double)nacc;
+          // pass B: carry from the threads before (the block's carry-in for thread 0)
+          if (t0 < t1) {
+            float2 carry = f2(0.f, 0.f), ap = f2(1.f, 0.f);
+            for (int s = 1; s <= tid + 1; ++s) {
+              if (tid - s >= 0) {
+                carry = fmac(ap, s_last[tid - s], carry);
+                const int lu = s_len[tid - s];
+                ap = mulc(ap, (lu <= kF32MaxTrunc) ? I.c2pow[lu] : f2(0.f, 0.f));
+                if (ap.x * ap.x + ap.y * ap.y < 2.2e-16f) break;  // (2^-26)^2
+              } else {
+                carry = fmac(ap, s_carry, carry);
+              }
+            }
+            const int nf = (I.kfix < (int)(t1 - t0)) ? I.kfix : (int)(t1 - t0);
+            const int kb = (int)(t0 - c0), klast = (int)(I.nx - 1 - c0), kend = (int)(t1 - 1 - c0);
+            float2 Sq[kF32MaxTrunc], Aq[kF32MaxTrunc];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) dn += __shfl_down_sync(0xffffffffu, dn, o);
-      if ((tid & 31) == 0) s_red[tid >> 5] = dn;
-      __syncthreads();
-      if (tid == 0) {
-        double t = 0.0;
-        for (int w = 0; w < kF32Threads / 32; ++w) t += s_red[w];
-        if (j_hi == I.nx && j_lo < j_hi) {
-          float2 l = row0[I.nx - 1];
-          t -= 0.5 * ((double)l.x * l.x + (double)l.y * l.y);
+            for (int u = 0; u < kF32MaxTrunc; ++u) {
+              const int k = kb + (u < nf ? u : nf - 1);
+              Sq[u] = oh[k];
+              Aq[u] = oe[k];
+            }
+            float2 ylast = y;
+#pragma unroll
+            for (int u = 0; u < kF32MaxTrunc; ++u) {
+              if (u < nf) {
+                const int k = kb + u;
+                const float2 S = fmac(I.c2pow[u + 1], carry, Sq[u]);
+                float2 sv, e;
+                two_sum(Aq[u].x, S.x, sv.x, e.x);
+                two_sum(Aq[u].y, S.y, sv.y, e.y);
+                oh[k] = sv;
+                oe[k] = e;
+                const float wt = (k == klast) ? 0.5f : 1.0f;
+                nacc = fmaf(wt * sv.x, sv.x, nacc);
+                nacc = fmaf(wt * sv.y, sv.y, nacc);
+                if (k == kend) ylast = sv;
+              }
+            }
+            if (t1 == c1) s_carry = ylast;  // carry into the next block
+            if (gen && snap)
+              for (int64_t jj = t0; jj < t1; ++jj) snap[jj] = row0[jj];
+          }
+          __syncthreads();  // block results complete
+          if (!gen) {  // coalesced stores of the block
+            float2* r0 = row0 + c0;
+            float2* ew = es_wr + c0 + 1;
+            float2* sp = snap ? snap + c0 : nullptr;
+            for (int k = tid; k < (int)len; k += kF32Threads) {
+              const float2 h = o_hi[k];
+              r0[k] = h;
+              ew[k] = o_e[k];
+              if (sp) sp[k] = h;
+            }
+            __syncthreads();  // staging and output buffers free for the next block
+          }
+          c0 = c1;
         }
-        I.partials[(n & 1) * kClusterMax + rank] = t;
-      }
-      cluster_sync_all();
-      if (rank == 0 && tid == 0) {
-        const cd ex = I.C * (I.phitab[n] * I.etab[n]);
-        double t = 0.5 * cabs2(ex);
-        for (unsigned b = 0; b < C; ++b) t += I.partials[(n & 1) * kClusterMax + b];
-        I.norms[n] = I.delta * t;
+
+        // norm: FP32 within a warp, FP64 across warps and CTAs
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nacc += __shfl_down_sync(0xffffffffu, nacc, o);
+        if ((tid & 31) == 0) s_red[n & 1][tid >> 5] = nacc;
+        if (solo) __syncthreads();
+        else cluster_sync_all();
+        if (rank_e == 0 && tid == 0) {
+          double t = I.bnorm[n];
+          for (unsigned bb = 0; bb < C_e; ++bb)
+            for (int w = 0; w < kF32Threads / 32; ++w) {
+              const float* pw = &s_red[n & 1][w];
+              t += (double)(solo ? *pw : ld_dsmem_f32(pw, bb));
+            }
+          I.norms[n] = I.delta * t;
+        }
+        slot = (slot + 1 == I.R) ? 0 : slot + 1;
+        if (snap_ctr >= 0) snap_ctr = (snap_ctr == I.tstep) ? 0 : snap_ctr + 1;
       }
     }
-    // save a_lo of the last row for the next launch
-    {
-      float2* es = ((n_end - 1) & 1) ? es1 : es0;
-      for (int64_t j = j_lo + 1 + tid; j <= j_hi; j += kF32Threads)
-        if (j - 1 < I.nx) I.lo_g[j - 1] = es[j - j_lo];
-    }
-    cluster_sync_all();  // lo_g and lo_edge complete before any CTA moves on
+    cluster_sync_all();  // the item is complete before any CTA of the cluster moves on
   }
-  (void)sync;
 }
 
-// FP32 copies of the boundary tables an instance's march reads
+// FP32 copies of the boundary tables an instance's march reads, and the
+// boundary column psi(-a, n delta) = C phi(-a - n delta) e(n delta) as an FP32
+// hi/lo pair with its FP64 trapezoid end term delta-free (1/2)|psi|^2
 __global__ void k_tables32(InstDesc I, const cd* detab, const cd* rowscal) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   auto cv = [](cd v) { return make_float2((float)v.re, (float)v.im); };
   if (i < I.nt) {
+    const cd ex = I.C * (I.phitab[i] * I.etab[i]);
+    const float2 hi = cv(ex);
+    const_cast<float2*>(I.bnd32)[2 * i] = hi;
+    const_cast<float2*>(I.bnd32)[2 * i + 1] = make_float2((float)(ex.re - (double)hi.x), (float)(ex.im - (double)hi.y));
+    const_cast<double*>(I.bnorm)[i] = 0.5 * cabs2(ex);
     const_cast<float2*>(I.etab32)[i] = cv(I.etab[i]);
     const_cast<float2*>(I.rowscal32)[2 * i] = cv(rowscal[2 * i]);
     const_cast<float2*>(I.rowscal32)[2 * i + 1] = cv(rowscal[2 * i + 1]);
@@ -442,7 +621,7 @@ cudaError_t launch_advance(InstDesc* insts, int ninst, int64_t rows, cudaStream_
   return cudaGetLastError();
 }
 
-size_t march_f32c_smem(int64_t cols) { return sizeof(float2) * (size_t)(3 * cols + 2); }
+size_t march_f32c_smem(int64_t cols) { return sizeof(float2) * (size_t)(8 * kStageCols + cols); }
 
 int march_f32c_max_clusters(int csize, size_t smem) {
   cudaError_t e = cudaFuncSetAttribute(k_march_f32c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -464,7 +643,7 @@ int march_f32c_max_clusters(int csize, size_t smem) {
   return e == cudaSuccess ? n : -1;
 }
 
-cudaError_t launch_march_f32c(const InstDesc* insts, const int* order, int ninst, unsigned int* queue,
+cudaError_t launch_march_f32c(const InstDesc* insts, const WorkItem* items, int nitems, unsigned int* queue,
                               SyncWords* sync, int nclusters, int csize, size_t smem, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nclusters * csize);
@@ -478,7 +657,7 @@ cudaError_t launch_march_f32c(const InstDesc* insts, const int* order, int ninst
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_march_f32c, insts, order, ninst, queue, sync);
+  return cudaLaunchKernelEx(&cfg, k_march_f32c, insts, items, nitems, queue, sync);
 }
 
 }  // namespace fdtd

@@ -99,3 +99,24 @@ def jittered(base: Workload, seed: int, n: int) -> list[Workload]:
         al = g.uniform(0.5, 2.0)
         out.append(base.with_(k=base.omega0 + dk, alpha=al, name=f"{base.name}_jit{i}"))
     return out
+
+
+def batch(seed: int = 1707, n: int = 256, nx_lo: int = 1 << 10, nx_hi: int = 1 << 16, d_lo: int = 10,
+          d_hi: int = 2000) -> list[Workload]:
+    """Seeded batch of uneven instances, two identical Gaussian photons each:
+    nx log-uniform in [nx_lo, nx_hi], nt = nx, D uniform in [d_lo, d_hi] rounded
+    to even and redrawn until D <= nx/2, Gamma a ~ U[0.1, 5], k0 a ~ U[0, 2 pi),
+    sigma ~ U[0.5, 10]/Gamma, Gamma = 1, pulse centred 8 sigma left of x = -a."""
+    g = SplitMix64(seed)
+    out = []
+    for i in range(n):
+        nx = int(round(math.exp(g.uniform(math.log(nx_lo), math.log(nx_hi)))))
+        while True:
+            D = 2 * int(round(g.uniform(d_lo, d_hi) / 2))
+            if D <= nx // 2:
+                break
+        ga = g.uniform(0.1, 5.0)
+        k0a = g.uniform(0.0, 2 * PI)
+        sigma = g.uniform(0.5, 10.0)
+        out.append(gauss_pair(nx, nx, D=D, a=ga, gamma=1.0, k0a=k0a, sigma=sigma, name=f"batch{seed}_{i}"))
+    return out
