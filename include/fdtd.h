@@ -238,6 +238,69 @@ fdtd_status fdtd_march_noalloc(const fdtd_params* p, void* cuda_stream, void* ro
 /* Size in bytes of the built-in scratch of fdtd_march_noalloc. */
 size_t fdtd_noalloc_max_bytes(void);
 
+/* ---- surrogate network -----------------------------------------------------
+ * The paper has no counterpart: a multilayer perceptron maps a few physical
+ * parameters of an instance (for example Gamma a, k0 a, the photon width and
+ * centre) to quantities the march produces (the norm N(t) of Sec. 3 on a time
+ * grid, a sub-sampled outgoing amplitude), trained on march output.  The march
+ * stays the fallback and the judge of the network's error.
+ *
+ * Network: dims[0] inputs -> GELU(affine) -> ... -> affine -> dims[n_layers]
+ * outputs, GELU(z) = z/2 (1 + erf(z/sqrt 2)).  Parameters, one block per layer
+ * l = 0..n_layers-1, in this order: W_l [dims[l+1]][dims[l]] row-major, then
+ * b_l [dims[l+1]].  All arrays below are device memory owned by the caller,
+ * sized fdtd_mlp_param_count elements.  Arithmetic: layer 0 (dims[0] <= 64
+ * inputs) in FP32 on the CUDA cores; every other layer on the tensor cores with
+ * BF16 weights (params_bf16) and BF16 activations, FP32 accumulation, FP32
+ * bias and pre-activations; Adam updates the FP32 masters (params) and then
+ * refreshes params_bf16.
+ * Shapes: 2 <= n_layers <= 7; dims[1..n_layers] multiples of 64; batch a
+ * multiple of 64.  Calls queue work on cuda_stream and return without
+ * synchronising.  Errors: FDTD_ERR_INVALID_ARG (shape rule, NULL pointer,
+ * struct_size), FDTD_ERR_CUDA.
+ */
+typedef struct fdtd_mlp {
+  uint32_t struct_size; /* sizeof(fdtd_mlp) */
+  int32_t n_layers;     /* affine layers                                  */
+  int32_t dims[8];      /* widths: dims[0] inputs .. dims[n_layers] outputs */
+  float* params;        /* FP32 master parameters                          */
+  void* params_bf16;    /* BF16 copy of params, same layout                */
+  float* grads;         /* FP32 gradient of the loss, same layout          */
+  float* adam_m;        /* Adam first moment (zero before step 1)          */
+  float* adam_v;        /* Adam second moment (zero before step 1)         */
+} fdtd_mlp;
+
+/* Number of parameters (floats) of the network. */
+fdtd_status fdtd_mlp_param_count(const fdtd_mlp* net, int64_t* count);
+
+/* Device scratch (bytes) that forward / train_step need for `batch` rows. */
+fdtd_status fdtd_mlp_workspace_bytes(const fdtd_mlp* net, int32_t batch, size_t* bytes);
+
+/* params_bf16 <- round-to-nearest BF16 of params. */
+fdtd_status fdtd_mlp_sync_bf16(const fdtd_mlp* net, void* cuda_stream);
+
+/* y[batch][dims[n_layers]] (FP32) = network(x[batch][dims[0]] (FP32)).
+ * ws: device scratch of fdtd_mlp_workspace_bytes, 256-byte aligned. */
+fdtd_status fdtd_mlp_forward(const fdtd_mlp* net, const float* x, int32_t batch, float* y, void* ws,
+                             void* cuda_stream);
+
+/* One training step on the mean squared error
+ *   loss = (1 / (batch * dims[n_layers])) sum (y - target)^2:
+ * forward, backward into net->grads (every parameter), and, when lr > 0, one
+ * Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias correction with the 1-based
+ * `step`).  *loss (device, FP32) receives the loss of the forward pass.  With
+ * lr = 0 the weights stay untouched (gradient only; adam_m / adam_v may be
+ * NULL). */
+fdtd_status fdtd_mlp_train_step(const fdtd_mlp* net, const float* x, const float* target, int32_t batch, float lr,
+                                int32_t step, void* ws, float* loss, void* cuda_stream);
+
+/* The surrogate's GEMM on its own: C[M][N] (FP32, row-major, device) =
+ * sum_k A(m,k) B(k,n), A and B BF16 device arrays with A(m,k) = A[m lda + k]
+ * (ta = 0) or A[k lda + m] (ta = 1), B(k,n) = B[n ldb + k] (tb = 0) or
+ * B[k ldb + n] (tb = 1).  M, N multiples of 64, K a multiple of 32. */
+fdtd_status fdtd_gemm_bf16(const void* A, const void* B, float* C, int32_t M, int32_t N, int32_t K, int32_t lda,
+                           int32_t ldb, int32_t ta, int32_t tb, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,9 @@ READ_ROW, READ_NORMS, READ_SNAPSHOTS, READ_ETABLE, READ_ROWS_DONE = range(5)
 
 EXPORTS = ["fdtd_plan", "fdtd_bind_workspace", "fdtd_set_boundary", "fdtd_march", "fdtd_readout",
            "fdtd_readout_bytes", "fdtd_destroy", "fdtd_status_string", "fdtd_last_error", "fdtd_gamma_star",
-           "fdtd_march_noalloc", "fdtd_noalloc_max_bytes", "fdtd_readout_instance", "fdtd_readout_instance_bytes"]
+           "fdtd_march_noalloc", "fdtd_noalloc_max_bytes", "fdtd_readout_instance", "fdtd_readout_instance_bytes",
+           "fdtd_mlp_param_count", "fdtd_mlp_workspace_bytes", "fdtd_mlp_sync_bf16", "fdtd_mlp_forward",
+           "fdtd_mlp_train_step", "fdtd_gemm_bf16"]
 
 
 class FdtdParams(ctypes.Structure):
@@ -50,6 +52,19 @@ class FdtdParams(ctypes.Structure):
         ("center", ctypes.c_double),
         ("tstep", ctypes.c_int32),
         ("rows_per_launch", ctypes.c_int32),
+    ]
+
+
+class FdtdMlp(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32),
+        ("n_layers", ctypes.c_int32),
+        ("dims", ctypes.c_int32 * 8),
+        ("params", ctypes.c_void_p),
+        ("params_bf16", ctypes.c_void_p),
+        ("grads", ctypes.c_void_p),
+        ("adam_m", ctypes.c_void_p),
+        ("adam_v", ctypes.c_void_p),
     ]
 
 
@@ -90,8 +105,17 @@ def lib() -> ctypes.CDLL:
         L.fdtd_readout_instance_bytes.restype = i64
         L.fdtd_noalloc_max_bytes.argtypes = []
         L.fdtd_noalloc_max_bytes.restype = sz
+        mp = ctypes.POINTER(FdtdMlp)
+        L.fdtd_mlp_param_count.argtypes = [mp, ctypes.POINTER(i64)]
+        L.fdtd_mlp_workspace_bytes.argtypes = [mp, i32, ctypes.POINTER(sz)]
+        L.fdtd_mlp_sync_bf16.argtypes = [mp, vp]
+        L.fdtd_mlp_forward.argtypes = [mp, vp, i32, vp, vp, vp]
+        L.fdtd_mlp_train_step.argtypes = [mp, vp, vp, i32, ctypes.c_float, i32, vp, vp, vp]
+        L.fdtd_gemm_bf16.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, i32, i32, vp]
         for f in ("fdtd_plan", "fdtd_bind_workspace", "fdtd_set_boundary", "fdtd_march", "fdtd_readout",
-                  "fdtd_gamma_star", "fdtd_march_noalloc", "fdtd_readout_instance"):
+                  "fdtd_gamma_star", "fdtd_march_noalloc", "fdtd_readout_instance", "fdtd_mlp_param_count",
+                  "fdtd_mlp_workspace_bytes", "fdtd_mlp_sync_bf16", "fdtd_mlp_forward", "fdtd_mlp_train_step",
+                  "fdtd_gemm_bf16"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -166,6 +190,41 @@ def fdtd_march_noalloc(params: FdtdParams, stream: int | None, row_out_ptr: int,
 
 def fdtd_noalloc_max_bytes() -> int:
     return int(lib().fdtd_noalloc_max_bytes())
+
+
+def fdtd_mlp_param_count(net: FdtdMlp) -> int:
+    n = ctypes.c_int64()
+    _check(lib().fdtd_mlp_param_count(ctypes.byref(net), ctypes.byref(n)), None, "fdtd_mlp_param_count")
+    return n.value
+
+
+def fdtd_mlp_workspace_bytes(net: FdtdMlp, batch: int) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().fdtd_mlp_workspace_bytes(ctypes.byref(net), batch, ctypes.byref(n)), None,
+           "fdtd_mlp_workspace_bytes")
+    return n.value
+
+
+def fdtd_mlp_sync_bf16(net: FdtdMlp, stream: int | None = None):
+    _check(lib().fdtd_mlp_sync_bf16(ctypes.byref(net), ctypes.c_void_p(stream or 0)), None, "fdtd_mlp_sync_bf16")
+
+
+def fdtd_mlp_forward(net: FdtdMlp, x_ptr: int, batch: int, y_ptr: int, ws_ptr: int, stream: int | None = None):
+    _check(lib().fdtd_mlp_forward(ctypes.byref(net), ctypes.c_void_p(x_ptr), batch, ctypes.c_void_p(y_ptr),
+                                  ctypes.c_void_p(ws_ptr), ctypes.c_void_p(stream or 0)), None, "fdtd_mlp_forward")
+
+
+def fdtd_mlp_train_step(net: FdtdMlp, x_ptr: int, target_ptr: int, batch: int, lr: float, step: int, ws_ptr: int,
+                        loss_ptr: int, stream: int | None = None):
+    _check(lib().fdtd_mlp_train_step(ctypes.byref(net), ctypes.c_void_p(x_ptr), ctypes.c_void_p(target_ptr), batch,
+                                     lr, step, ctypes.c_void_p(ws_ptr), ctypes.c_void_p(loss_ptr),
+                                     ctypes.c_void_p(stream or 0)), None, "fdtd_mlp_train_step")
+
+
+def fdtd_gemm_bf16(a_ptr: int, b_ptr: int, c_ptr: int, M: int, N: int, K: int, lda: int, ldb: int, ta: int, tb: int,
+                   stream: int | None = None):
+    _check(lib().fdtd_gemm_bf16(ctypes.c_void_p(a_ptr), ctypes.c_void_p(b_ptr), ctypes.c_void_p(c_ptr), M, N, K, lda,
+                                ldb, ta, tb, ctypes.c_void_p(stream or 0)), None, "fdtd_gemm_bf16")
 
 
 # ---- convenience ------------------------------------------------------------

@@ -21,7 +21,7 @@ def F():
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "fdtd.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(fdtd_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(fdtd_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_exports_match_header(F):
@@ -81,3 +81,60 @@ def test_null_plan_calls(F):
     assert L.fdtd_gamma_star(None, None, None, -1, None) == F.ERR_INVALID_ARG
     L.fdtd_destroy(None)
     assert L.fdtd_status_string(F.ERR_TIMEOUT) == b"device-side wait timed out"
+
+
+def test_mlp_struct_layout(F, tmp_path):
+    import subprocess
+    fields = [f for f, _ in F.FdtdMlp._fields_]
+    prog = "#include <stdio.h>\n#include <stddef.h>\n#include \"fdtd.h\"\nint main(void){printf(\"%zu\\n\", sizeof(fdtd_mlp));"
+    prog += "".join(f'printf("%zu\\n", offsetof(fdtd_mlp, {f}));' for f in fields) + "return 0;}"
+    src = tmp_path / "mlp_layout.c"
+    src.write_text(prog)
+    exe = tmp_path / "mlp_layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    assert out[0] == ctypes.sizeof(F.FdtdMlp)
+    assert out[1:] == [getattr(F.FdtdMlp, f).offset for f in fields]
+
+
+def _net(F, dims, ptrs=True):
+    net = F.FdtdMlp()
+    net.struct_size = ctypes.sizeof(F.FdtdMlp)
+    net.n_layers = len(dims) - 1
+    for i, d in enumerate(dims):
+        net.dims[i] = d
+    if ptrs:
+        net.params = net.params_bf16 = 256
+    return net
+
+
+def test_mlp_param_count_and_workspace(F):
+    # host-only calls: 4 -> 512 x 4 -> 8704 has 4*512+512 + 3*(512*512+512) + 512*8704+8704 parameters
+    net = _net(F, [4, 512, 512, 512, 512, 8704])
+    assert F.fdtd_mlp_param_count(net) == 4 * 512 + 512 + 3 * (512 * 512 + 512) + 512 * 8704 + 8704
+    ws = F.fdtd_mlp_workspace_bytes(net, 256)
+    assert ws >= 256 * (4 * 512 * 6 + 8704 * 8)
+
+
+@pytest.mark.parametrize("dims,batch", [([4, 512, 100], 64), ([4, 512, 512], 32), ([4, 512], 64),
+                                        ([65, 512, 512], 64), ([4, 0, 64], 64)])
+def test_mlp_rejects_bad_shapes(F, dims, batch):
+    net = _net(F, dims)
+    n = ctypes.c_size_t()
+    assert F.lib().fdtd_mlp_workspace_bytes(ctypes.byref(net), batch, ctypes.byref(n)) == F.ERR_INVALID_ARG
+
+
+def test_mlp_rejects_null_and_size(F):
+    L = F.lib()
+    net = _net(F, [4, 64, 64], ptrs=False)
+    n = ctypes.c_size_t()
+    assert L.fdtd_mlp_workspace_bytes(ctypes.byref(net), 64, ctypes.byref(n)) == F.ERR_INVALID_ARG
+    net = _net(F, [4, 64, 64])
+    net.struct_size = 12
+    assert L.fdtd_mlp_workspace_bytes(ctypes.byref(net), 64, ctypes.byref(n)) == F.ERR_INVALID_ARG
+    net = _net(F, [4] + [64] * 7)
+    assert L.fdtd_mlp_workspace_bytes(ctypes.byref(net), 64, ctypes.byref(n)) == F.OK
+    net.n_layers = 8  # more layers than dims[] can describe
+    assert L.fdtd_mlp_workspace_bytes(ctypes.byref(net), 64, ctypes.byref(n)) == F.ERR_INVALID_ARG
+    assert L.fdtd_gemm_bf16(None, None, None, 64, 64, 32, 32, 32, 0, 0, None) == F.ERR_INVALID_ARG
+    assert L.fdtd_gemm_bf16(256, 256, 256, 64, 64, 48, 48, 48, 0, 0, None) == F.ERR_INVALID_ARG

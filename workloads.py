@@ -120,3 +120,33 @@ def batch(seed: int = 1707, n: int = 256, nx_lo: int = 1 << 10, nx_hi: int = 1 <
         sigma = g.uniform(0.5, 10.0)
         out.append(gauss_pair(nx, nx, D=D, a=ga, gamma=1.0, k0a=k0a, sigma=sigma, name=f"batch{seed}_{i}"))
     return out
+
+
+# ---- surrogate training and held-out draws ----------------------------------
+# One fixed grid for every draw, so that outputs line up across instances:
+# delta = 0.05 / Gamma, 1024 marched columns x 1024 rows (t up to 51.2 / Gamma).
+SURR_DELTA = 0.05
+SURR_NX = 1024
+SURR_NT = 1024
+# feature ranges: Gamma a, k0 a, sigma Gamma, extra lead s Gamma (pulse centre at -a - 6 sigma - s)
+SURR_RANGES = ((0.25, 2.5), (0.0, PI), (1.0, 3.0), (0.0, 4.0))
+
+
+def surrogate_draw(seed: int, n: int) -> tuple[list[Workload], list[tuple[float, float, float, float]]]:
+    """Seeded (workload, feature) pairs for the surrogate.  Gamma = 1; D = 2a/delta
+    rounded to even (a is then D delta / 2); k = w0 = k0 (resonant); two identical
+    Gaussian photons of width sigma, centred 6 sigma + s left of x = -a."""
+    g = SplitMix64(seed)
+    ws, feats = [], []
+    for i in range(n):
+        ga = g.uniform(*SURR_RANGES[0])
+        k0a = g.uniform(*SURR_RANGES[1])
+        sig = g.uniform(*SURR_RANGES[2])
+        s = g.uniform(*SURR_RANGES[3])
+        D = max(2, 2 * int(round(ga / SURR_DELTA)))
+        a = 0.5 * D * SURR_DELTA
+        w = gauss_pair(SURR_NX, SURR_NT, D=D, a=a, gamma=1.0, k0a=k0a, sigma=sig, lead=6.0 + s / sig,
+                       name=f"surr{seed}_{i}")
+        ws.append(w)
+        feats.append((a, k0a, sig, s))
+    return ws, feats
