@@ -255,7 +255,7 @@ size_t fdtd_noalloc_max_bytes(void);
  * bias and pre-activations; Adam updates the FP32 masters (params) and then
  * refreshes params_bf16.
  * Shapes: 2 <= n_layers <= 7; dims[1..n_layers] multiples of 64; batch a
- * multiple of 64.  Calls queue work on cuda_stream and return without
+ * multiple of 64; params_bf16 16-byte aligned; ws 256-byte aligned.  Calls queue work on cuda_stream and return without
  * synchronising.  Errors: FDTD_ERR_INVALID_ARG (shape rule, NULL pointer,
  * struct_size), FDTD_ERR_CUDA.
  */
@@ -295,11 +295,17 @@ fdtd_status fdtd_mlp_train_step(const fdtd_mlp* net, const float* x, const float
                                 int32_t step, void* ws, float* loss, void* cuda_stream);
 
 /* The surrogate's GEMM on its own: C[M][N] (FP32, row-major, device) =
- * sum_k A(m,k) B(k,n), A and B BF16 device arrays with A(m,k) = A[m lda + k]
- * (ta = 0) or A[k lda + m] (ta = 1), B(k,n) = B[n ldb + k] (tb = 0) or
- * B[k ldb + n] (tb = 1).  M, N multiples of 64, K a multiple of 32. */
+ * sum_k A[m lda + k] B[n ldb + k], A and B BF16 device arrays with K
+ * contiguous (16-byte aligned, lda and ldb multiples of 8, >= K).  M, N
+ * multiples of 64, K a multiple of 32.  Runs on the tensor cores (tcgen05,
+ * FP32 accumulation in tensor memory). */
 fdtd_status fdtd_gemm_bf16(const void* A, const void* B, float* C, int32_t M, int32_t N, int32_t K, int32_t lda,
-                           int32_t ldb, int32_t ta, int32_t tb, void* cuda_stream);
+                           int32_t ldb, void* cuda_stream);
+
+/* Synchronise cuda_stream and report (then clear) a GEMM wait that ran out of
+ * time on this device since the last call: FDTD_ERR_TIMEOUT, else FDTD_OK.
+ * The kernels skip their output after such a timeout instead of hanging. */
+fdtd_status fdtd_mlp_status(void* cuda_stream);
 
 #ifdef __cplusplus
 }

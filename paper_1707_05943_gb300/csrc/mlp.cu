@@ -1,31 +1,46 @@
-// mlp.cu -- BF16 tensor-core kernels of the surrogate network: a multilayer
-// perceptron inputs -> GELU hidden layers -> linear outputs, trained with Adam
-// on FP32 master weights.  GEMMs run on the tensor cores with mma.sync
-// m16n8k16 (BF16 operands, FP32 accumulation) from shared-memory tiles; the
-// first layer (4 inputs) and the element-wise steps run on the CUDA cores.
+// mlp.cu -- kernels of the surrogate network: a multilayer perceptron
+// inputs -> GELU hidden layers -> linear outputs, trained with Adam on FP32
+// master weights.
+//
+// GEMMs run on the fifth-generation tensor cores: every product is cast as
+// C[m][n] = sum_k A[m][k] B[n][k] with both operands K-contiguous BF16 in
+// global memory.  A CTA owns a 128 x 128 tile of C; cp.async stages 128 x 64
+// slices of A and B into shared memory (three stages) in the canonical
+// K-major core-matrix layout (8 rows x 16 bytes per core matrix, no swizzle);
+// one thread issues tcgen05.mma kind::f16 (M 128, N 128, K 16 per
+// instruction) into an FP32 accumulator in tensor memory and commits each
+// stage to an mbarrier; the epilogue reads the accumulator back with
+// tcgen05.ld (thread = row) and fuses bias, GELU, GELU' and the BF16 casts,
+// writing transposed copies where backpropagation needs the other operand
+// order.  Layer 0 (a handful of inputs) and the element-wise steps run on the
+// CUDA cores.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
+
+#include <mutex>
 
 #include "fdtd_internal.cuh"
 
 namespace fdtd {
 
-// ---- GEMM: C[M,N] = sum_k A(m,k) B(k,n) --------------------------------------
-// A(m,k) = A[m*lda + k] (ta = 0) or A[k*lda + m] (ta = 1); B(k,n) = B[n*ldb + k]
-// (tb = 0) or B[k*ldb + n] (tb = 1).  M, N multiples of 64, K of 32.
+__device__ int g_mlp_status;  // 1: an mbarrier wait of the GEMM ran out
+
 enum Epi { EPI_GELU = 0, EPI_LINEAR = 1, EPI_DGELU = 2, EPI_F32 = 3 };
 
-struct GemmArgs {
-  const __nv_bfloat16* A;
-  const __nv_bfloat16* B;
-  int M, N, K, lda, ldb, ta, tb;
+struct NtArgs {
+  const __nv_bfloat16* A;  // [M][lda], K contiguous
+  const __nv_bfloat16* B;  // [N][ldb], K contiguous
+  int M, N, K, lda, ldb;
   int epi;
-  const float* bias;        // EPI_GELU / EPI_LINEAR: bias[n]
-  float* out_f32;           // EPI_GELU: pre-activation z; EPI_LINEAR / EPI_F32: result
-  __nv_bfloat16* out_bf16;  // EPI_GELU: gelu(z); EPI_DGELU: acc * gelu'(zprev)
-  const float* zprev;       // EPI_DGELU: pre-activation of the layer below [M,N]
-  int ldo;
+  const float* bias;          // EPI_GELU / EPI_LINEAR: bias[n]
+  float* out_f32;             // EPI_GELU: pre-activation; EPI_LINEAR / EPI_F32: result   [M][ldo]
+  __nv_bfloat16* out_bf16;    // EPI_GELU: gelu(z); EPI_DGELU: acc * gelu'(zprev)        [M][ldo]
+  __nv_bfloat16* out_bf16_t;  // optional transposed copy of out_bf16                     [N][ldt]
+  const float* zprev;         // EPI_DGELU: [M][ldo]
+  int ldo, ldt;
+  long long spin;             // clock cycles an mbarrier wait may take before giving up
 };
 
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
@@ -33,91 +48,220 @@ __device__ __forceinline__ float dgelu(float z) {
   return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
 
-constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
+constexpr int TM = 128, TN = 128, TK = 64, NSTAGE = 3;
+constexpr int kTileBytes = TM * TK * 2;                       // 16 KB per operand slice
+constexpr int kGemmSmem = NSTAGE * 2 * kTileBytes + 1024;     // + alignment slack
+constexpr uint32_t kTmemCols = TN;                            // FP32 accumulator columns
+// instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9,
+// 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at 24-28
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                            ((uint32_t)(TM >> 4) << 24);
+// core-matrix strides of a staged slice: K-adjacent core matrices 128 B apart,
+// 8-row groups (TK / 8) * 128 B apart
+constexpr uint32_t kLBO = 128, kSBO = (TK / 8) * 128;
 
-__global__ void __launch_bounds__(128) k_gemm_bf16(const GemmArgs g) {
-  __shared__ __align__(16) __nv_bfloat16 As[GBM][GBK + GPAD];
-  __shared__ __align__(16) __nv_bfloat16 Bs[GBN][GBK + GPAD];  // [n][k]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;  // warp tile 32 x 32
-  const int gid = lane >> 2, tig = lane & 3;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-  for (int k0 = 0; k0 < g.K; k0 += GBK) {
-    // tiles into shared memory, reading along the contiguous global dimension
-    for (int idx = tid; idx < GBM * GBK; idx += 128) {
-      int m, k;
-      if (!g.ta) { m = idx / GBK; k = idx % GBK; }
-      else { k = idx / GBM; m = idx % GBM; }
-      As[m][k] = g.ta ? g.A[(size_t)(k0 + k) * g.lda + (m0 + m)] : g.A[(size_t)(m0 + m) * g.lda + (k0 + k)];
-      int n, kk;
-      if (!g.tb) { n = idx / GBK; kk = idx % GBK; }
-      else { kk = idx / GBN; n = idx % GBN; }
-      Bs[n][kk] = g.tb ? g.B[(size_t)(k0 + kk) * g.ldb + (n0 + n)] : g.B[(size_t)(n0 + n) * g.ldb + (k0 + kk)];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int ks = 0; ks < GBK; ks += 16) {
-      unsigned a[2][4], b[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r = wm + i * 16 + gid;
-        a[i][0] = *reinterpret_cast<const unsigned*>(&As[r][ks + 2 * tig]);
-        a[i][1] = *reinterpret_cast<const unsigned*>(&As[r + 8][ks + 2 * tig]);
-        a[i][2] = *reinterpret_cast<const unsigned*>(&As[r][ks + 2 * tig + 8]);
-        a[i][3] = *reinterpret_cast<const unsigned*>(&As[r + 8][ks + 2 * tig + 8]);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = wn + j * 8 + gid;
-        b[j][0] = *reinterpret_cast<const unsigned*>(&Bs[c][ks + 2 * tig]);
-        b[j][1] = *reinterpret_cast<const unsigned*>(&Bs[c][ks + 2 * tig + 8]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          asm volatile(
-              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-              "{%0,%1,%2,%3};\n"
-              : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
-              : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]), "r"(b[j][1]));
-    }
-    __syncthreads();
-  }
-  // epilogue: accumulator element (row gid / gid+8, cols 2 tig, 2 tig + 1)
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int m = m0 + wm + i * 16 + gid + ((r >= 2) ? 8 : 0);
-        const int n = n0 + wn + j * 8 + 2 * tig + (r & 1);
-        const size_t o = (size_t)m * g.ldo + n;
-        float v = acc[i][j][r];
-        if (g.epi == EPI_GELU) {
-          v += g.bias[n];
-          g.out_f32[o] = v;
-          g.out_bf16[o] = __float2bfloat16(gelu(v));
-        } else if (g.epi == EPI_LINEAR) {
-          g.out_f32[o] = v + g.bias[n];
-        } else if (g.epi == EPI_DGELU) {
-          g.out_bf16[o] = __float2bfloat16(v * dgelu(g.zprev[o]));
-        } else {
-          g.out_f32[o] = v;
-        }
-      }
+// shared-memory matrix descriptor: start, leading and stride byte offsets (>> 4),
+// descriptor version 1 at bits 46-47, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((kLBO >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((kSBO >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
-// first layer: z[b,n] = sum_k x[b,k] W[n,k] + bias[n] (K = in_dim, tiny), FP32
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ bool mbar_done(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; false when the limit ran out
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, long long spin) {
+  const long long t0 = clock64();
+  while (!mbar_done(a, parity))
+    if (clock64() - t0 > spin) return false;
+  return true;
+}
+
+#define TC_LD32(taddr, v)                                                                                            \
+  asm volatile(                                                                                                      \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19," \
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"                                                   \
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),  \
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),       \
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),      \
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])                    \
+      : "r"(taddr))
+
+__global__ void __launch_bounds__(128) k_gemm_nt_tc(const NtArgs g) {
+  extern __shared__ unsigned char dsmem[];
+  __shared__ __align__(8) uint64_t mbar[NSTAGE];
+  __shared__ uint32_t tmem_sh;
+  __shared__ int abort_sh;
+  unsigned char* sbase = (unsigned char*)(((uintptr_t)dsmem + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(&tmem_sh)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < NSTAGE; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&mbar[s])));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    abort_sh = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_sh;
+  const int nk = (g.K + TK - 1) / TK;
+
+  // one 128 x 64 slice of A and of B into stage s: 16-byte chunk q of a slice
+  // is row r = (q & 7) + 8 (q >> 6), K-chunk c = (q >> 3) & 7, so that 8
+  // consecutive threads fill one core matrix (conflict-free) and 4 chunks of a
+  // row stay contiguous in global memory; rows >= M (N) and chunks >= K are zero
+  auto load_slice = [&](int kt, int s) {
+    const uint32_t sA = su32(sbase + (size_t)s * 2 * kTileBytes), sB = sA + kTileBytes;
+    const int k0 = kt * TK;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int q = tid + 128 * i;
+      const int r = (q & 7) + 8 * (q >> 6), c = (q >> 3) & 7;
+      const uint32_t off = (uint32_t)(((r >> 3) * 8 + c) * 128 + (r & 7) * 16);
+      const int k = k0 + 8 * c;
+      const bool okA = (m0 + r) < g.M && k < g.K;
+      const bool okB = (n0 + r) < g.N && k < g.K;
+      cp_async16(sA + off, okA ? (const void*)(g.A + (size_t)(m0 + r) * g.lda + k) : (const void*)g.A, okA ? 16 : 0);
+      cp_async16(sB + off, okB ? (const void*)(g.B + (size_t)(n0 + r) * g.ldb + k) : (const void*)g.B, okB ? 16 : 0);
+    }
+  };
+
+  bool bad = false;
+#pragma unroll
+  for (int s = 0; s < NSTAGE - 1; ++s) {
+    if (s < nk) load_slice(s, s);
+    cp_async_commit();
+  }
+  for (int kt = 0; kt < nk; ++kt) {
+    const int s = kt % NSTAGE;
+    cp_async_wait<NSTAGE - 2>();
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && !abort_sh) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t sA = su32(sbase + (size_t)s * 2 * kTileBytes), sB = sA + kTileBytes;
+#pragma unroll
+      for (int kk = 0; kk < TK / 16; ++kk) {
+        const uint64_t da = sdesc(sA + kk * 256), db = sdesc(sB + kk * 256);
+        const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(kIdesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       su32(&mbar[s]))
+                   : "memory");
+    }
+    // refill the stage of slice kt - 1 once its MMAs have read it
+    const int nt = kt + NSTAGE - 1;
+    if (nt < nk) {
+      const int sp = nt % NSTAGE;
+      const uint32_t par = (uint32_t)(((kt - 1) / NSTAGE) & 1);
+      if (kt >= 1 && !bad && !mbar_wait(su32(&mbar[sp]), par, g.spin)) {
+        bad = true;
+        atomicExch(&g_mlp_status, 1);
+      }
+      if (!bad) load_slice(nt, sp);
+    }
+    cp_async_commit();
+    if (bad) abort_sh = 1;  // read by the issuing thread after the next barrier
+  }
+  cp_async_wait<0>();
+  // the last commit covers every MMA of this CTA
+  if (!bad && nk > 0) {
+    const int s = (nk - 1) % NSTAGE;
+    if (!mbar_wait(su32(&mbar[s]), (uint32_t)(((nk - 1) / NSTAGE) & 1), g.spin)) {
+      bad = true;
+      atomicExch(&g_mlp_status, 1);
+    }
+  }
+  if (bad) abort_sh = 1;
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+
+  if (!abort_sh) {
+    const int m = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int cb = 0; cb < TN; cb += 32) {
+      uint32_t v[32];
+      TC_LD32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      const int nb = n0 + cb;
+      if (nb >= g.N || m >= g.M) continue;
+      float f[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(v[j]);
+      const size_t o = (size_t)m * g.ldo + nb;
+      if (g.epi == EPI_GELU || g.epi == EPI_LINEAR) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) f[j] += __ldg(g.bias + nb + j);
+      }
+      if (g.epi == EPI_GELU || g.epi == EPI_LINEAR || g.epi == EPI_F32) {
+#pragma unroll
+        for (int j = 0; j < 32; j += 4)
+          *reinterpret_cast<float4*>(g.out_f32 + o + j) = make_float4(f[j], f[j + 1], f[j + 2], f[j + 3]);
+      }
+      if (g.epi == EPI_GELU || g.epi == EPI_DGELU) {
+        if (g.epi == EPI_GELU) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) f[j] = gelu(f[j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; j += 4) {
+            const float4 z = *reinterpret_cast<const float4*>(g.zprev + o + j);
+            f[j] *= dgelu(z.x);
+            f[j + 1] *= dgelu(z.y);
+            f[j + 2] *= dgelu(z.z);
+            f[j + 3] *= dgelu(z.w);
+          }
+        }
+        __align__(16) __nv_bfloat16 h[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) h[j] = __float2bfloat16(f[j]);
+#pragma unroll
+        for (int j = 0; j < 32; j += 8)
+          *reinterpret_cast<uint4*>(g.out_bf16 + o + j) = *reinterpret_cast<const uint4*>(h + j);
+        if (g.out_bf16_t) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) g.out_bf16_t[(size_t)(nb + j) * g.ldt + m] = h[j];
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
+}
+
+// ---- CUDA-core kernels ----------------------------------------------------------
+
+// first layer: z[b,n] = sum_k x[b,k] W[n,k] + bias[n] (K = inputs, tiny), FP32
 __global__ void k_layer0_fwd(const float* x, const float* W, const float* bias, int B, int K, int N, float* z,
                              __nv_bfloat16* a) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -145,14 +289,21 @@ __global__ void k_bias_grad_bf16(const __nv_bfloat16* dz, int B, int N, float* d
   for (int b = 0; b < B; ++b) s += __bfloat162float(dz[b * N + n]);
   db[n] = s;
 }
-// mean-squared error: dy = 2 (y - t) / (B N), loss accumulated in FP32 per block
+__global__ void k_bias_grad_f32(const float* dz, int B, int N, float* db) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float s = 0.f;
+  for (int b = 0; b < B; ++b) s += dz[b * N + n];
+  db[n] = s;
+}
+// mean squared error: dy = 2 (y - t) / (B N) (BF16 and FP32), loss summed per block in FP32
 __global__ void k_mse(const float* y, const float* t, int total, float scale, __nv_bfloat16* dy, float* dy32,
                       float* loss) {
   __shared__ float red[256];
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  float d = 0.f, l = 0.f;
+  float l = 0.f;
   if (i < total) {
-    d = y[i] - t[i];
+    const float d = y[i] - t[i];
     l = d * d;
     dy[i] = __float2bfloat16(2.f * d * scale);
     dy32[i] = 2.f * d * scale;
@@ -165,14 +316,21 @@ __global__ void k_mse(const float* y, const float* t, int total, float scale, __
   }
   if (threadIdx.x == 0) atomicAdd(loss, red[0] * scale);
 }
-__global__ void k_bias_grad_f32(const float* dz, int B, int N, float* db) {
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
-  float s = 0.f;
-  for (int b = 0; b < B; ++b) s += dz[b * N + n];
-  db[n] = s;
+// out[c][r] = in[r][c] for a rows x cols BF16 matrix, 32 x 32 tiles through shared memory
+__global__ void k_transpose_bf16(const __nv_bfloat16* in, __nv_bfloat16* out, int rows, int cols) {
+  __shared__ __nv_bfloat16 t[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) t[i][threadIdx.x] = in[(size_t)r * cols + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[(size_t)c * rows + r] = t[threadIdx.x][i];
+  }
 }
-// Adam on FP32 masters; BF16 copies of the weights refreshed
+// Adam on FP32 masters (Kingma & Ba, bias-corrected)
 __global__ void k_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2,
                        float eps, float c1, float c2) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -189,9 +347,22 @@ __global__ void k_to_bf16(const float* p, __nv_bfloat16* q, int64_t n) {
   if (i < n) q[i] = __float2bfloat16(p[i]);
 }
 
-static cudaError_t gemm(const GemmArgs& g, cudaStream_t s) {
-  dim3 grid(g.N / GBN, g.M / GBM);
-  k_gemm_bf16<<<grid, 128, 0, s>>>(g);
+static cudaError_t gemm_nt(NtArgs g, cudaStream_t s) {
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(k_gemm_nt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+  });
+  if (attr != cudaSuccess) return attr;
+  g.spin = 2000000000LL;  // about a second at the SM clock
+  dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM);
+  k_gemm_nt_tc<<<grid, 128, kGemmSmem, s>>>(g);
+  return cudaGetLastError();
+}
+
+static cudaError_t transpose(const __nv_bfloat16* in, __nv_bfloat16* out, int rows, int cols, cudaStream_t s) {
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+  k_transpose_bf16<<<grid, dim3(32, 8), 0, s>>>(in, out, rows, cols);
   return cudaGetLastError();
 }
 
@@ -213,23 +384,30 @@ void layer_offsets(const fdtd_mlp* d, int64_t* offW, int64_t* offb, int64_t* tot
   *total = o;
 }
 
-fdtd_status check(const fdtd_mlp* d, int batch) {
-  if (!d || d->struct_size != sizeof(fdtd_mlp) || d->n_layers < 2 || d->n_layers > 7) return FDTD_ERR_INVALID_ARG;
-  if (batch <= 0 || batch % 64) return FDTD_ERR_INVALID_ARG;
+bool shape_ok(const fdtd_mlp* d) {
+  if (!d || d->struct_size != sizeof(fdtd_mlp) || d->n_layers < 2 || d->n_layers > 7) return false;
   for (int l = 1; l <= d->n_layers; ++l)
-    if (d->dims[l] <= 0 || d->dims[l] % 64) return FDTD_ERR_INVALID_ARG;
-  if (d->dims[0] <= 0 || d->dims[0] > 64) return FDTD_ERR_INVALID_ARG;
+    if (d->dims[l] <= 0 || d->dims[l] % 64) return false;
+  return d->dims[0] > 0 && d->dims[0] <= 64;
+}
+
+fdtd_status check(const fdtd_mlp* d, int batch) {
+  if (!shape_ok(d) || batch <= 0 || batch % 64) return FDTD_ERR_INVALID_ARG;
   if (!d->params || !d->params_bf16) return FDTD_ERR_INVALID_ARG;
   return FDTD_OK;
 }
 
-// workspace: per layer z (FP32) and a (BF16) of [batch, width]; output y; dy (bf16, f32); dz buffers
+// workspace: per hidden layer z (FP32), a and a^T (BF16); output y; dz and dz^T
+// (two of each, BF16); dy in FP32; one transposed weight matrix
 struct Ws {
   float* z[8];
   __nv_bfloat16* a[8];
+  __nv_bfloat16* at[8];
   float* y;
   __nv_bfloat16* dz[2];
+  __nv_bfloat16* dzt[2];
   float* dy32;
+  __nv_bfloat16* wt;
 };
 size_t ws_layout(const fdtd_mlp* d, int batch, char* base, Ws* w) {
   size_t off = 0;
@@ -239,50 +417,74 @@ size_t ws_layout(const fdtd_mlp* d, int batch, char* base, Ws* w) {
     return p;
   };
   int maxw = 0;
+  size_t maxW = 0;
   for (int l = 1; l <= d->n_layers; ++l) maxw = maxw > d->dims[l] ? maxw : d->dims[l];
+  for (int l = 1; l < d->n_layers; ++l) {
+    const size_t e = (size_t)d->dims[l + 1] * d->dims[l];
+    maxW = maxW > e ? maxW : e;
+  }
   for (int l = 0; l < d->n_layers - 1; ++l) {
     w->z[l] = (float*)take(sizeof(float) * (size_t)batch * d->dims[l + 1]);
     w->a[l] = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * (size_t)batch * d->dims[l + 1]);
+    w->at[l] = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * (size_t)batch * d->dims[l + 1]);
   }
   w->y = (float*)take(sizeof(float) * (size_t)batch * d->dims[d->n_layers]);
-  w->dz[0] = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * (size_t)batch * maxw);
-  w->dz[1] = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * (size_t)batch * maxw);
+  for (int i = 0; i < 2; ++i) {
+    w->dz[i] = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * (size_t)batch * maxw);
+    w->dzt[i] = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * (size_t)batch * maxw);
+  }
   w->dy32 = (float*)take(sizeof(float) * (size_t)batch * d->dims[d->n_layers]);
+  w->wt = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * maxW);
   return off;
 }
 
-cudaError_t forward(const fdtd_mlp* d, const float* x, int batch, const Ws& w, cudaStream_t s) {
+cudaError_t forward(const fdtd_mlp* d, const float* x, int batch, const Ws& w, bool keep_t, cudaStream_t s) {
   int64_t offW[8], offb[8], total;
   layer_offsets(d, offW, offb, &total);
   const __nv_bfloat16* wb = static_cast<const __nv_bfloat16*>(d->params_bf16);
   const int N0 = d->dims[1], K0 = d->dims[0];
   k_layer0_fwd<<<(batch * N0 + 255) / 256, 256, 0, s>>>(x, d->params + offW[0], d->params + offb[0], batch, K0, N0,
                                                         w.z[0], w.a[0]);
+  if (keep_t) {
+    cudaError_t e = transpose(w.a[0], w.at[0], batch, N0, s);
+    if (e != cudaSuccess) return e;
+  }
   for (int l = 1; l < d->n_layers; ++l) {
-    GemmArgs g = {};
+    NtArgs g = {};
     g.A = w.a[l - 1];
-    g.B = wb + offW[l];
+    g.lda = d->dims[l];
+    g.B = wb + offW[l];  // W_l [n][k]
+    g.ldb = d->dims[l];
     g.M = batch;
     g.N = d->dims[l + 1];
     g.K = d->dims[l];
-    g.lda = d->dims[l];
-    g.ldb = d->dims[l];
-    g.ta = 0;
-    g.tb = 0;  // B(k,n) = W[n][k]
     g.bias = d->params + offb[l];
     g.ldo = g.N;
+    g.ldt = batch;
     if (l < d->n_layers - 1) {
       g.epi = EPI_GELU;
       g.out_f32 = w.z[l];
       g.out_bf16 = w.a[l];
+      g.out_bf16_t = keep_t ? w.at[l] : nullptr;
     } else {
       g.epi = EPI_LINEAR;
       g.out_f32 = w.y;
     }
-    cudaError_t e = gemm(g, s);
+    cudaError_t e = gemm_nt(g, s);
     if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
+}
+
+// BF16 weight blocks of layers >= 1 start where the FP32 ones do, so their byte
+// offsets are 2 * the float offsets: they must be 16-byte aligned for cp.async
+bool weights_aligned(const fdtd_mlp* d) {
+  int64_t offW[8], offb[8], total;
+  layer_offsets(d, offW, offb, &total);
+  if ((uintptr_t)d->params_bf16 & 15) return false;
+  for (int l = 1; l < d->n_layers; ++l)
+    if ((offW[l] * 2) & 15) return false;
+  return true;
 }
 
 }  // namespace
@@ -298,7 +500,7 @@ fdtd_status fdtd_mlp_param_count(const fdtd_mlp* d, int64_t* count) {
 
 fdtd_status fdtd_mlp_workspace_bytes(const fdtd_mlp* d, int32_t batch, size_t* bytes) {
   fdtd_status st = check(d, batch);
-  if (st != FDTD_OK) return st;
+  if (st != FDTD_OK || !bytes) return FDTD_ERR_INVALID_ARG;
   Ws w;
   *bytes = ws_layout(d, batch, nullptr, &w);
   return FDTD_OK;
@@ -315,11 +517,11 @@ fdtd_status fdtd_mlp_sync_bf16(const fdtd_mlp* d, void* stream) {
 fdtd_status fdtd_mlp_forward(const fdtd_mlp* d, const float* x, int32_t batch, float* y, void* ws, void* stream) {
   fdtd_status st = check(d, batch);
   if (st != FDTD_OK) return st;
-  if (!x || !y || !ws) return FDTD_ERR_INVALID_ARG;
+  if (!x || !y || !ws || ((uintptr_t)ws & 255) || !weights_aligned(d)) return FDTD_ERR_INVALID_ARG;
   Ws w;
   ws_layout(d, batch, static_cast<char*>(ws), &w);
   cudaStream_t s = (cudaStream_t)stream;
-  if (forward(d, x, batch, w, s) != cudaSuccess) return FDTD_ERR_CUDA;
+  if (forward(d, x, batch, w, false, s) != cudaSuccess) return FDTD_ERR_CUDA;
   const size_t nout = (size_t)batch * d->dims[d->n_layers];
   if (cudaMemcpyAsync(y, w.y, sizeof(float) * nout, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return FDTD_ERR_CUDA;
   return FDTD_OK;
@@ -329,59 +531,59 @@ fdtd_status fdtd_mlp_train_step(const fdtd_mlp* d, const float* x, const float* 
                                 int32_t step, void* ws, float* loss, void* stream) {
   fdtd_status st = check(d, batch);
   if (st != FDTD_OK) return st;
-  if (!x || !target || !ws || !loss || !d->grads || (lr > 0 && (!d->adam_m || !d->adam_v)) || step < 1)
+  if (!x || !target || !ws || ((uintptr_t)ws & 255) || !loss || !d->grads ||
+      (lr > 0 && (!d->adam_m || !d->adam_v)) || step < 1 || !weights_aligned(d))
     return FDTD_ERR_INVALID_ARG;
   Ws w;
   ws_layout(d, batch, static_cast<char*>(ws), &w);
   cudaStream_t s = (cudaStream_t)stream;
-  if (forward(d, x, batch, w, s) != cudaSuccess) return FDTD_ERR_CUDA;
+  if (forward(d, x, batch, w, true, s) != cudaSuccess) return FDTD_ERR_CUDA;
   int64_t offW[8], offb[8], total;
   layer_offsets(d, offW, offb, &total);
   const __nv_bfloat16* wb = static_cast<const __nv_bfloat16*>(d->params_bf16);
   const int L = d->n_layers, Nout = d->dims[L];
   const int tot = batch * Nout;
-  cudaMemsetAsync(loss, 0, sizeof(float), s);
+  if (cudaMemsetAsync(loss, 0, sizeof(float), s) != cudaSuccess) return FDTD_ERR_CUDA;
   k_mse<<<(tot + 255) / 256, 256, 0, s>>>(w.y, target, tot, 1.f / (float)tot, w.dz[0], w.dy32, loss);
-  // output layer (linear): dW = dy^T a_{L-2}, db = sum dy
+  if (transpose(w.dz[0], w.dzt[0], batch, Nout, s) != cudaSuccess) return FDTD_ERR_CUDA;
   int cur = 0;
   for (int l = L - 1; l >= 1; --l) {
     const int N = d->dims[l + 1], K = d->dims[l];
-    // weight gradient: dW[n,k] = sum_b dz[b,n] a[b,k]
-    GemmArgs gw = {};
-    gw.A = w.dz[cur];
-    gw.ta = 1;
-    gw.lda = N;  // A(m=n, k=b) = dz[b*N + n]
-    gw.B = w.a[l - 1];
-    gw.tb = 1;
-    gw.ldb = K;  // B(k=b, n=k) = a[b*K + k]
+    // weight gradient: dW[n][k] = sum_b dz[b][n] a[b][k] = sum_b dz^T[n][b] a^T[k][b]
+    NtArgs gw = {};
+    gw.A = w.dzt[cur];
+    gw.lda = batch;
+    gw.B = w.at[l - 1];
+    gw.ldb = batch;
     gw.M = N;
     gw.N = K;
     gw.K = batch;
     gw.epi = EPI_F32;
     gw.out_f32 = d->grads + offW[l];
     gw.ldo = K;
-    if (gemm(gw, s) != cudaSuccess) return FDTD_ERR_CUDA;
+    if (gemm_nt(gw, s) != cudaSuccess) return FDTD_ERR_CUDA;
     if (l == L - 1) k_bias_grad_f32<<<(N + 127) / 128, 128, 0, s>>>(w.dy32, batch, N, d->grads + offb[l]);
     else k_bias_grad_bf16<<<(N + 127) / 128, 128, 0, s>>>(w.dz[cur], batch, N, d->grads + offb[l]);
-    // data gradient through GELU of the layer below: dz_{l-1} = (dz_l W_l) * gelu'(z_{l-1})
-    GemmArgs gd = {};
+    // data gradient through GELU of the layer below:
+    // dz'[b][k] = gelu'(z[b][k]) sum_n dz[b][n] W[n][k], with W^T[k][n] as the K-contiguous operand
+    if (transpose(wb + offW[l], w.wt, N, K, s) != cudaSuccess) return FDTD_ERR_CUDA;
+    NtArgs gd = {};
     gd.A = w.dz[cur];
-    gd.ta = 0;
-    gd.lda = N;  // A(m=b, k=n) = dz[b*N + n]
-    gd.B = wb + offW[l];
-    gd.tb = 1;
-    gd.ldb = K;  // B(k=n, n=k) = W[n*K + k]
+    gd.lda = N;
+    gd.B = w.wt;
+    gd.ldb = N;
     gd.M = batch;
     gd.N = K;
     gd.K = N;
     gd.epi = EPI_DGELU;
     gd.zprev = w.z[l - 1];
     gd.out_bf16 = w.dz[cur ^ 1];
+    gd.out_bf16_t = w.dzt[cur ^ 1];
     gd.ldo = K;
-    if (gemm(gd, s) != cudaSuccess) return FDTD_ERR_CUDA;
+    gd.ldt = batch;
+    if (gemm_nt(gd, s) != cudaSuccess) return FDTD_ERR_CUDA;
     cur ^= 1;
   }
-  // first layer
   {
     const int N = d->dims[1], K = d->dims[0];
     k_layer0_wgrad<<<(N * K + 255) / 256, 256, 0, s>>>(w.dz[cur], x, batch, K, N, d->grads + offW[0]);
@@ -399,9 +601,11 @@ fdtd_status fdtd_mlp_train_step(const fdtd_mlp* d, const float* x, const float* 
 }
 
 fdtd_status fdtd_gemm_bf16(const void* A, const void* B, float* C, int32_t M, int32_t N, int32_t K, int32_t lda,
-                           int32_t ldb, int32_t ta, int32_t tb, void* stream) {
-  if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0 || M % 64 || N % 64 || K % 32) return FDTD_ERR_INVALID_ARG;
-  GemmArgs g = {};
+                           int32_t ldb, void* stream) {
+  if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0 || M % 64 || N % 64 || K % 32 || lda < K || ldb < K ||
+      lda % 8 || ldb % 8 || ((uintptr_t)A & 15) || ((uintptr_t)B & 15) || ((uintptr_t)C & 15))
+    return FDTD_ERR_INVALID_ARG;
+  NtArgs g = {};
   g.A = static_cast<const __nv_bfloat16*>(A);
   g.B = static_cast<const __nv_bfloat16*>(B);
   g.M = M;
@@ -409,12 +613,22 @@ fdtd_status fdtd_gemm_bf16(const void* A, const void* B, float* C, int32_t M, in
   g.K = K;
   g.lda = lda;
   g.ldb = ldb;
-  g.ta = ta;
-  g.tb = tb;
   g.epi = EPI_F32;
   g.out_f32 = C;
   g.ldo = N;
-  return gemm(g, (cudaStream_t)stream) == cudaSuccess ? FDTD_OK : FDTD_ERR_CUDA;
+  return gemm_nt(g, (cudaStream_t)stream) == cudaSuccess ? FDTD_OK : FDTD_ERR_CUDA;
+}
+
+fdtd_status fdtd_mlp_status(void* stream) {
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return FDTD_ERR_CUDA;
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_mlp_status, sizeof v) != cudaSuccess) return FDTD_ERR_CUDA;
+  if (v) {
+    const int zero = 0;
+    if (cudaMemcpyToSymbol(g_mlp_status, &zero, sizeof zero) != cudaSuccess) return FDTD_ERR_CUDA;
+    return FDTD_ERR_TIMEOUT;
+  }
+  return FDTD_OK;
 }
 
 }  // extern "C"

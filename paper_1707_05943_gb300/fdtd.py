@@ -32,7 +32,7 @@ EXPORTS = ["fdtd_plan", "fdtd_bind_workspace", "fdtd_set_boundary", "fdtd_march"
            "fdtd_readout_bytes", "fdtd_destroy", "fdtd_status_string", "fdtd_last_error", "fdtd_gamma_star",
            "fdtd_march_noalloc", "fdtd_noalloc_max_bytes", "fdtd_readout_instance", "fdtd_readout_instance_bytes",
            "fdtd_mlp_param_count", "fdtd_mlp_workspace_bytes", "fdtd_mlp_sync_bf16", "fdtd_mlp_forward",
-           "fdtd_mlp_train_step", "fdtd_gemm_bf16"]
+           "fdtd_mlp_train_step", "fdtd_gemm_bf16", "fdtd_mlp_status"]
 
 
 class FdtdParams(ctypes.Structure):
@@ -111,11 +111,12 @@ def lib() -> ctypes.CDLL:
         L.fdtd_mlp_sync_bf16.argtypes = [mp, vp]
         L.fdtd_mlp_forward.argtypes = [mp, vp, i32, vp, vp, vp]
         L.fdtd_mlp_train_step.argtypes = [mp, vp, vp, i32, ctypes.c_float, i32, vp, vp, vp]
-        L.fdtd_gemm_bf16.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, i32, i32, vp]
+        L.fdtd_gemm_bf16.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, vp]
+        L.fdtd_mlp_status.argtypes = [vp]
         for f in ("fdtd_plan", "fdtd_bind_workspace", "fdtd_set_boundary", "fdtd_march", "fdtd_readout",
                   "fdtd_gamma_star", "fdtd_march_noalloc", "fdtd_readout_instance", "fdtd_mlp_param_count",
                   "fdtd_mlp_workspace_bytes", "fdtd_mlp_sync_bf16", "fdtd_mlp_forward", "fdtd_mlp_train_step",
-                  "fdtd_gemm_bf16"):
+                  "fdtd_gemm_bf16", "fdtd_mlp_status"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -221,10 +222,14 @@ def fdtd_mlp_train_step(net: FdtdMlp, x_ptr: int, target_ptr: int, batch: int, l
                                      ctypes.c_void_p(stream or 0)), None, "fdtd_mlp_train_step")
 
 
-def fdtd_gemm_bf16(a_ptr: int, b_ptr: int, c_ptr: int, M: int, N: int, K: int, lda: int, ldb: int, ta: int, tb: int,
+def fdtd_gemm_bf16(a_ptr: int, b_ptr: int, c_ptr: int, M: int, N: int, K: int, lda: int, ldb: int,
                    stream: int | None = None):
     _check(lib().fdtd_gemm_bf16(ctypes.c_void_p(a_ptr), ctypes.c_void_p(b_ptr), ctypes.c_void_p(c_ptr), M, N, K, lda,
-                                ldb, ta, tb, ctypes.c_void_p(stream or 0)), None, "fdtd_gemm_bf16")
+                                ldb, ctypes.c_void_p(stream or 0)), None, "fdtd_gemm_bf16")
+
+
+def fdtd_mlp_status(stream: int | None = None):
+    _check(lib().fdtd_mlp_status(ctypes.c_void_p(stream or 0)), None, "fdtd_mlp_status")
 
 
 # ---- convenience ------------------------------------------------------------

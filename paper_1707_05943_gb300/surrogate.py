@@ -186,6 +186,16 @@ class Surrogate:
         self.dims = list(dims)
         self.ranges = ranges
 
+    def _standardise(self, Y: np.ndarray):
+        """Per-output mean and scale of the training targets; the scale is the
+        output's standard deviation, floored at 5% of the largest one of its
+        group (N(t) or amplitude) so that near-constant outputs are not blown up."""
+        self.mu = Y.mean(axis=0)
+        sd = Y.std(axis=0)
+        for lo, hi in ((0, N_TIMES), (N_TIMES, Y.shape[1])):
+            sd[lo:hi] = np.maximum(sd[lo:hi], 0.05 * sd[lo:hi].max())
+        self.sd = sd
+
     def fit(self, X: np.ndarray, Y: np.ndarray, steps: int = 4000, batch: int = 256, lr: float = 1e-3,
             lr_min: float = 1e-5) -> TrainLog:
         """Adam with a cosine learning-rate decay; contiguous minibatches of a
@@ -194,8 +204,9 @@ class Surrogate:
         n = (X.shape[0] // batch) * batch
         if n == 0:
             raise ValueError("need at least one full batch of training data")
+        self._standardise(Y)
         Xd = torch.from_numpy(np.ascontiguousarray(X[:n], np.float32)).cuda()
-        Yd = torch.from_numpy(np.ascontiguousarray(Y[:n], np.float32)).cuda()
+        Yd = torch.from_numpy(np.ascontiguousarray((Y[:n] - self.mu) / self.sd, np.float32)).cuda()
         nb = n // batch
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -223,7 +234,7 @@ class Surrogate:
         for k, net in enumerate(self.nets):
             for s in range(0, npad, batch):
                 net.forward(Xd[s:s + batch], Ys[k, s:s + batch])
-        Y = Ys[:, :n].cpu().numpy().astype(np.float64)
+        Y = Ys[:, :n].cpu().numpy().astype(np.float64) * self.sd + self.mu
         return Y.mean(axis=0), (Y.max(axis=0) - Y.min(axis=0)).max(axis=1)
 
     def answer(self, workloads, feats, tol: float = 1e-3):

@@ -136,5 +136,7 @@ def test_mlp_rejects_null_and_size(F):
     assert L.fdtd_mlp_workspace_bytes(ctypes.byref(net), 64, ctypes.byref(n)) == F.OK
     net.n_layers = 8  # more layers than dims[] can describe
     assert L.fdtd_mlp_workspace_bytes(ctypes.byref(net), 64, ctypes.byref(n)) == F.ERR_INVALID_ARG
-    assert L.fdtd_gemm_bf16(None, None, None, 64, 64, 32, 32, 32, 0, 0, None) == F.ERR_INVALID_ARG
-    assert L.fdtd_gemm_bf16(256, 256, 256, 64, 64, 48, 48, 48, 0, 0, None) == F.ERR_INVALID_ARG
+    assert L.fdtd_gemm_bf16(None, None, None, 64, 64, 32, 32, 32, None) == F.ERR_INVALID_ARG
+    assert L.fdtd_gemm_bf16(256, 256, 256, 64, 64, 48, 48, 48, None) == F.ERR_INVALID_ARG   # K % 32
+    assert L.fdtd_gemm_bf16(256, 256, 256, 64, 64, 32, 36, 32, None) == F.ERR_INVALID_ARG   # lda % 8
+    assert L.fdtd_gemm_bf16(264, 256, 256, 64, 64, 32, 32, 32, None) == F.ERR_INVALID_ARG   # A not 16-aligned
