@@ -154,7 +154,9 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "small"])
+    ap.add_argument("--workload", default="large", choices=["large", "small", "batch", "precision", "surrogate"])
+    ap.add_argument("--batch-n", type=int, default=256, help="instances of the seeded batch")
+    ap.add_argument("--compare-f64", action="store_true", help="also march the batch in FP64, one plan each")
     ap.add_argument("--rows", type=int, default=0, help="march only this many rows (profiling)")
     ap.add_argument("--nx", type=int, default=0, help="march only this many columns (profiling)")
     ap.add_argument("--D", type=int, default=0, help="use this D at the same delta (profiling)")
@@ -165,6 +167,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
 
+    if args.workload in ("batch", "precision", "surrogate"):
+        if args.impl == "reference":
+            run_reference(args, W.PRECISION if args.workload != "batch" else W.batch(n=args.batch_n)[0])
+        else:
+            run_variant(args)
+        return
     w = W.LARGE if args.workload == "large" else W.SMALL
     if args.rows:
         w = w.with_(nt=args.rows, name=f"{w.name}_rows{args.rows}")
@@ -250,6 +258,10 @@ def main():
 
     # dominant kernel: the march launches (full-size ones)
     full = [(a.elapsed_time(b), n) for a, b, n in events if n == rpl] or [(a.elapsed_time(b), n) for a, b, n in events]
+    # DRAM bytes per update from one ncu capture of k_march_f64 (2^20 columns, D = 100, 4096 rows:
+    # 137.9 GB per launch); the D = 2000 launch moves the same bytes per update (both delay rows
+    # lie far outside L2), so the figure is scaled by the updates of one launch
+    ncu_bytes_per_update = 32.1
     avg_ms = sum(t for t, _ in full) / len(full)
     rows_l = full[0][1]
     peaks, src = load_peaks()
@@ -262,7 +274,9 @@ def main():
             "unit": "TFLOP/s", "frac": ach_tf / FP64_NOMINAL_TFLOPS,
             "peak_source": "GB300 nominal dense FP64 1.25 TFLOP/s (no FP64 figure in MEASURED_PEAKS.json)",
             "flops_per_update": FLOPS_PER_UPDATE_F64, "updates_per_launch": upd_launch,
-            "launch_ms": avg_ms, "traffic": None,
+            "launch_ms": avg_ms, "traffic": ncu_bytes_per_update * upd_launch,
+            "traffic_source": "ncu dram__bytes_read+write of k_march_f64 at nx 2^20, D 100 (32.1 B/update), "
+                              "scaled to this launch's updates",
             "hbm": {"achieved": ach_gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                     "frac": ach_gbs / peaks.get("hbm_gbs", 6800.0), "bytes_per_update": BYTES_PER_UPDATE_F64,
                     "peak_source": src}}
@@ -316,6 +330,171 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def _clock_ok(clocks):
+    return clocks
+
+
+def run_variant(args):
+    """The complex64 compensated march on the seeded batch or the precision
+    instance, or the surrogate network's training and inference; one JSON line."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    from paper_1707_05943_gb300 import build, fdtd as F
+    build.build()
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    peaks, src = load_peaks()
+    if args.workload == "surrogate":
+        return run_surrogate(args, peaks, src)
+
+    ws_list = W.batch(n=args.batch_n) if args.workload == "batch" else [W.PRECISION]
+    name = f"batch1707_n{len(ws_list)}" if args.workload == "batch" else W.PRECISION.name
+
+    def cfg(w, prec, tstep=-1):
+        return F.Config(nx=w.nx, nt=w.nt, D=w.D, delta=w.delta, gamma=w.gamma, omega0=w.omega0, k=w.k,
+                        init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center, tstep=tstep,
+                        precision=prec, rows_per_launch=0).c()
+
+    arr = (F.FdtdParams * len(ws_list))(*[cfg(w, F.F32_COMP) for w in ws_list])
+    nbytes, plan = ctypes.c_size_t(), ctypes.c_void_p()
+    F._check(F.lib().fdtd_plan(arr, len(ws_list), None, ctypes.byref(nbytes), ctypes.byref(plan)), None, "plan")
+    buf = torch.empty(nbytes.value + 256, dtype=torch.uint8, device="cuda")
+    F.fdtd_bind_workspace(plan, (buf.data_ptr() + 255) // 256 * 256, nbytes.value)
+    rows = max(w.nt for w in ws_list)
+    updates = sum(w.updates for w in ws_list)
+    stream = torch.cuda.default_stream()
+    ev = []
+
+    def step(record=False):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        F.fdtd_set_boundary(plan)
+        e1.record(stream)
+        F.fdtd_march(plan, rows)
+        e2.record(stream)
+        if record:
+            ev.append((e0, e1, e2))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.start()
+    start.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = start.elapsed_time(stop)
+    t_bnd = sum(a.elapsed_time(b) for a, b, _ in ev) / len(ev)
+    t_march = sum(b.elapsed_time(c) for _, b, c in ev) / len(ev)
+    # error against the FP64 march (parity-checked against the oracle) on up to 4 instances
+    pick = sorted(range(len(ws_list)), key=lambda i: ws_list[i].updates)[:4]
+    errs, nerrs = [], []
+    for i in pick:
+        w = ws_list[i]
+        last = np.empty(w.nx, np.complex64)
+        F.fdtd_readout_instance(plan, i, F.READ_ROW, last.ctypes.data, last.nbytes)
+        norms = np.empty(w.nt, np.float64)
+        F.fdtd_readout_instance(plan, i, F.READ_NORMS, norms.ctypes.data, norms.nbytes)
+        s64 = F.Solver(F.Config(nx=w.nx, nt=w.nt, D=w.D, delta=w.delta, gamma=w.gamma, omega0=w.omega0, k=w.k,
+                                init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center, tstep=-1))
+        s64.set_boundary()
+        s64.march(w.nt)
+        r64 = s64.read(F.READ_ROW)
+        n64 = s64.read(F.READ_NORMS)
+        s64.close()
+        r64 = np.asarray(r64).view(np.complex128) if np.asarray(r64).dtype != np.complex128 else np.asarray(r64)
+        errs.append(float(np.linalg.norm(last.astype(np.complex128) - r64) / max(np.linalg.norm(r64), 1e-300)))
+        nerrs.append(float(np.max(np.abs(norms - np.asarray(n64))) / max(np.max(np.abs(n64)), 1e-300)))
+    f64 = None
+    if args.compare_f64:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for w in ws_list:
+            s64 = F.Solver(F.Config(nx=w.nx, nt=w.nt, D=w.D, delta=w.delta, gamma=w.gamma, omega0=w.omega0,
+                                    k=w.k, init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center,
+                                    tstep=-1))
+            s64.set_boundary()
+            s64.march(w.nt)
+            s64.read(F.READ_NORMS)
+            s64.close()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        f64 = {"value": updates / dt, "unit": UNIT, "how": "same instances, one FP64 plan each, back to back "
+                                                           "(wall clock, plan + boundary + march + norms)"}
+    F.fdtd_destroy(plan)
+    ach = 16 * updates / (t_march * 1e-3) / 1e9
+    out = {"metric": METRIC, "value": updates * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c64-compensated (FP64 boundary and norms)",
+           "data": "synthetic",
+           "config": {"workload": name, "instances": len(ws_list), "updates_per_step": updates,
+                      "l2": "inputs larger than L2 (rings of all instances "
+                            f"{sum((w.D + 2) * w.nx * 8 for w in ws_list) / 1e9:.1f} GB)"},
+           "roofline": {"kernel": "k_march_f32c", "bound": "hbm", "achieved": ach, "peak": peaks.get("hbm_gbs"),
+                        "unit": "GB/s", "frac": ach / peaks.get("hbm_gbs", 6800.0), "traffic": None,
+                        "bytes_per_update": 16, "launch_ms": t_march, "peak_source": src},
+           "boundary_ms": t_bnd, "march_ms": t_march,
+           "error_vs_fp64": {"instances": pick, "last_row_rel_l2_max": max(errs), "norms_rel_max": max(nerrs)},
+           "clocks": clocks}
+    if f64:
+        out["fp64_same_instances"] = f64
+    print(json.dumps(out), flush=True)
+
+
+def run_surrogate(args, peaks, src):
+    """Training and inference throughput of one surrogate network (4 -> 512 x 4
+    GELU -> 8704, BF16 tensor cores) on random inputs of the surrogate's shape."""
+    import torch
+
+    from paper_1707_05943_gb300 import fdtd as F, surrogate as S
+    batch = 512
+    net = S.Net(S.DIMS, seed=1)
+    x = torch.rand(batch, 4, device="cuda") * 2 - 1
+    t = torch.randn(batch, S.N_OUT, device="cuda")
+    y = torch.empty(batch, S.N_OUT, device="cuda")
+    st = torch.cuda.ExternalStream(net.sp)
+    for _ in range(args.warmup * 10):
+        net.train_step(x, t, 1e-4)
+    torch.cuda.synchronize()
+    n_steps = 200 * args.steps
+    sampler = ClockSampler(0)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    sampler.start()
+    e0.record(st)
+    for _ in range(n_steps):
+        net.train_step(x, t, 1e-4)
+    e1.record(st)
+    for _ in range(n_steps):
+        net.forward(x, y)
+    e2.record(st)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    F.fdtd_mlp_status(net.sp)
+    ms_train = e0.elapsed_time(e1) / n_steps
+    ms_inf = e1.elapsed_time(e2) / n_steps
+    fl = 2 * batch * sum(S.DIMS[i] * S.DIMS[i + 1] for i in range(1, len(S.DIMS) - 1))
+    ach = 3 * fl / (ms_train * 1e-3) / 1e12
+    out = {"metric": "surrogate training samples/s (BF16 tensor cores)", "value": batch / (ms_train * 1e-3),
+           "unit": "samples/s", "n_gpus": 1, "steps": n_steps, "warmup": args.warmup * 10,
+           "ms_per_step": ms_train, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "bf16 (FP32 accumulation, FP32 master weights)", "data": "synthetic",
+           "config": {"workload": "surrogate_4x512x4_8704", "batch": batch,
+                      "l2": "weights and activations L2-resident (training step; no flush)"},
+           "inference": {"value": batch / (ms_inf * 1e-3), "unit": "samples/s", "ms_per_batch": ms_inf},
+           "roofline": {"kernel": "k_gemm_nt_tc (all GEMMs of the step)", "bound": "tensor", "achieved": ach,
+                        "peak": peaks.get("bf16_tflops"), "unit": "TFLOP/s",
+                        "frac": ach / peaks.get("bf16_tflops", 1900.0), "traffic": None, "peak_source": src},
+           "clocks": clocks}
+    print(json.dumps(out), flush=True)
 
 
 def solver_grid(s) -> int:

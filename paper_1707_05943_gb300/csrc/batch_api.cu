@@ -96,6 +96,7 @@ fdtd_status batch_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n, v
   P->off_desc = off;  off = align_up(off + sizeof(fdtd::InstDesc) * (size_t)n);
   P->off_order = off; off = align_up(off + sizeof(fdtd::WorkItem) * (size_t)n);
   P->off_queue = off; off = align_up(off + sizeof(unsigned int) * 4);
+  P->off_eargs = off; off = align_up(off + sizeof(fdtd::EtabArgs) * (size_t)n);
   int64_t cols = 0;
   for (int i = 0; i < n; ++i) {
     const fdtd_params& p = pin[i];
@@ -172,6 +173,9 @@ fdtd_status batch_set_boundary(fdtd_plan_s* P, int32_t source, const void* table
   cudaError_t e = cudaMemsetAsync(P->ws + P->off_sync, 0, sizeof(fdtd::SyncWords), s);
   if (e != cudaSuccess) return cuda_fail(P, e, "cudaMemsetAsync");
   std::vector<fdtd::InstDesc> desc(n);
+  std::vector<fdtd::BoundaryArgs> bargs(n);
+  std::vector<fdtd::EtabArgs> eargs(n);
+  int64_t max_nt = 0;
   const char* tab = static_cast<const char*>(table);
   for (int i = 0; i < n; ++i) {
     fdtd_batch_inst& b = P->inst[i];
@@ -208,7 +212,23 @@ fdtd_status batch_set_boundary(fdtd_plan_s* P, int32_t source, const void* table
     a.C = b.C;
     a.cs = b.cs;
     a.status = &at<fdtd::SyncWords>(P, P->off_sync)->status;
-    e = fdtd::launch_boundary(a, at<cd>(P, b.off_hscr), source == FDTD_BOUNDARY_ANALYTIC, s);
+    e = fdtd::launch_boundary_pre(a, s);
+    if (e != cudaSuccess) return cuda_fail(P, e, "boundary kernels");
+    bargs[i] = a;
+    eargs[i] = fdtd::etable_args(a, at<cd>(P, b.off_hscr));
+    max_nt = std::max<int64_t>(max_nt, p.nt);
+  }
+  // e(t) of every instance in one launch per pass (FP64)
+  if (source == FDTD_BOUNDARY_ANALYTIC) {
+    e = cudaMemcpyAsync(P->ws + P->off_eargs, eargs.data(), sizeof(fdtd::EtabArgs) * (size_t)n,
+                        cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = fdtd::launch_etable_batch(at<fdtd::EtabArgs>(P, P->off_eargs), n, max_nt, s);
+    if (e != cudaSuccess) return cuda_fail(P, e, "boundary e-tables");
+  }
+  for (int i = 0; i < n; ++i) {
+    fdtd_batch_inst& b = P->inst[i];
+    const fdtd_params& p = b.p;
+    e = fdtd::launch_boundary_post(bargs[i], s);
     if (e != cudaSuccess) return cuda_fail(P, e, "boundary kernels");
 
     fdtd::InstDesc& d = desc[i];

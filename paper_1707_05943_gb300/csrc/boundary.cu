@@ -16,6 +16,8 @@
 // regrouped).  For the Gaussian wavepacket F_j is integrated by composite
 // Gauss-Legendre over the part of [0,u] where the pulse is above e^-40.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <math.h>
 
 #include "fdtd_internal.cuh"
@@ -171,16 +173,9 @@ __device__ cd h_gauss(const BoundaryArgs& A, double tau, int panels) {
   return tot;
 }
 
-struct EtabArgs {
-  BoundaryArgs b;
-  cd* h;       // scratch for h(r delta) (two-photon classes)
-  int panels;
-};
-
 // pass 1: e(r delta) for stimulated emission, h(r delta) for the two-photon classes
-__global__ void k_etable_pass1(const EtabArgs E) {
+__device__ __forceinline__ void etable_row(const EtabArgs& E, int64_t r) {
   const BoundaryArgs& A = E.b;
-  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= A.nt) return;
   double t = r * A.delta;
   if (A.init_cond == FDTD_IC_STIM_EMISSION) {
@@ -191,15 +186,23 @@ __global__ void k_etable_pass1(const EtabArgs E) {
     E.h[r] = h_gauss(A, t, E.panels);
   }
 }
+__global__ void k_etable_pass1(const EtabArgs E) { etable_row(E, blockIdx.x * (int64_t)blockDim.x + threadIdx.x); }
+// every instance of a batch in one launch: blockIdx.y is the instance
+__global__ void k_etable_pass1_batch(const EtabArgs* Es) {
+  etable_row(Es[blockIdx.y], blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+}
 
 // pass 2: e(r delta) = h(r delta) - h((r-D) delta)
-__global__ void k_etable_pass2(const EtabArgs E) {
+__device__ __forceinline__ void etable_diff(const EtabArgs& E, int64_t r) {
   const BoundaryArgs& A = E.b;
-  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (r >= A.nt) return;
+  if (r >= A.nt || A.init_cond == FDTD_IC_STIM_EMISSION) return;
   cd v = E.h[r];
   if (r >= A.D) v = v - E.h[r - A.D];
   A.etab[r] = v;
+}
+__global__ void k_etable_pass2(const EtabArgs E) { etable_diff(E, blockIdx.x * (int64_t)blockDim.x + threadIdx.x); }
+__global__ void k_etable_pass2_batch(const EtabArgs* Es) {
+  etable_diff(Es[blockIdx.y], blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
 }
 
 // phi table and per-row source scalars.
@@ -292,7 +295,18 @@ static cudaError_t upload_gl(int dev) {
   return e;
 }
 
-cudaError_t launch_boundary(const BoundaryArgs& a, cd* hscratch, bool compute_etable, cudaStream_t s) {
+EtabArgs etable_args(const BoundaryArgs& a, cd* hscratch) {
+  EtabArgs E;
+  E.b = a;
+  E.h = hscratch;
+  // panels: 8 plus two per oscillation of e^{i(w0-k)v} across the pulse window
+  double win = 2.0 * sqrt(160.0) * a.sigma;
+  E.panels = 8 + 2 * (int)ceil(fabs(a.omega0 - a.k) * win / (2.0 * M_PI));
+  return E;
+}
+
+// tables that do not need e(t): phi table and per-row source scalars
+cudaError_t launch_boundary_pre(const BoundaryArgs& a, cudaStream_t s) {
   int dev = 0;
   cudaGetDevice(&dev);
   cudaError_t e = upload_gl(dev);
@@ -300,19 +314,41 @@ cudaError_t launch_boundary(const BoundaryArgs& a, cd* hscratch, bool compute_et
   const int T = 128;
   k_phitab<<<(unsigned)((a.nphi + T - 1) / T), T, 0, s>>>(a);
   k_rowscal<<<(unsigned)((a.nt + T - 1) / T), T, 0, s>>>(a);
-  if (compute_etable) {
-    EtabArgs E;
-    E.b = a;
-    E.h = hscratch;
-    // panels: 8 plus two per oscillation of e^{i(w0-k)v} across the pulse window
-    double win = 2.0 * sqrt(160.0) * a.sigma;
-    E.panels = 8 + 2 * (int)ceil(fabs(a.omega0 - a.k) * win / (2.0 * M_PI));
-    k_etable_pass1<<<(unsigned)((a.nt + 63) / 64), 64, 0, s>>>(E);
-    if (a.init_cond != FDTD_IC_STIM_EMISSION) k_etable_pass2<<<(unsigned)((a.nt + T - 1) / T), T, 0, s>>>(E);
+  return cudaGetLastError();
+}
+
+// e(t) of n instances whose EtabArgs sit in device memory, one launch per pass
+cudaError_t launch_etable_batch(const EtabArgs* dev_args, int n, int64_t max_nt, cudaStream_t s) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaError_t e = upload_gl(dev);
+  if (e != cudaSuccess || n <= 0) return e;
+  for (int i0 = 0; i0 < n; i0 += 65535) {  // grid.y limit
+    const unsigned m = (unsigned)std::min(65535, n - i0);
+    k_etable_pass1_batch<<<dim3((unsigned)((max_nt + 63) / 64), m), 64, 0, s>>>(dev_args + i0);
+    k_etable_pass2_batch<<<dim3((unsigned)((max_nt + 127) / 128), m), 128, 0, s>>>(dev_args + i0);
   }
+  return cudaGetLastError();
+}
+
+// tables that need e(t): the initial norm and the mirror-source differences
+cudaError_t launch_boundary_post(const BoundaryArgs& a, cudaStream_t s) {
+  const int T = 128;
   k_norm0<<<1, 1, 0, s>>>(a);
   k_detab<<<(unsigned)((a.nt + a.D + T - 1) / T), T, 0, s>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_boundary(const BoundaryArgs& a, cd* hscratch, bool compute_etable, cudaStream_t s) {
+  cudaError_t e = launch_boundary_pre(a, s);
+  if (e != cudaSuccess) return e;
+  if (compute_etable) {
+    const int T = 128;
+    EtabArgs E = etable_args(a, hscratch);
+    k_etable_pass1<<<(unsigned)((a.nt + 63) / 64), 64, 0, s>>>(E);
+    if (a.init_cond != FDTD_IC_STIM_EMISSION) k_etable_pass2<<<(unsigned)((a.nt + T - 1) / T), T, 0, s>>>(E);
+  }
+  return launch_boundary_post(a, s);
 }
 
 cudaError_t launch_gamma_star(const int32_t* n, const double* z, double* out, int64_t count, cudaStream_t s) {

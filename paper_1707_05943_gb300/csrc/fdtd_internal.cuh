@@ -174,7 +174,7 @@ struct fdtd_plan_s {
   // complex64 (batched) plans
   bool batched = false;
   std::vector<fdtd_batch_inst> inst;
-  size_t off_desc = 0, off_order = 0, off_queue = 0;
+  size_t off_desc = 0, off_order = 0, off_queue = 0, off_eargs = 0;
   int nitems = 0;
   int csize = 0, nclusters = 0;
   int64_t smem_cols = 0;
@@ -195,6 +195,16 @@ fdtd_status batch_readout(fdtd_plan_s* P, int32_t inst, int32_t kind, void* dst,
 namespace fdtd {
 // launchers (return cudaError_t)
 cudaError_t launch_boundary(const BoundaryArgs& a, cd* hscratch, bool compute_etable, cudaStream_t s);
+// the same work in three steps, so that a batch computes every e-table in one launch
+struct EtabArgs {
+  BoundaryArgs b;
+  cd* h;  // scratch for h(r delta) (two-photon classes)
+  int panels;
+};
+EtabArgs etable_args(const BoundaryArgs& a, cd* hscratch);
+cudaError_t launch_boundary_pre(const BoundaryArgs& a, cudaStream_t s);
+cudaError_t launch_etable_batch(const EtabArgs* dev_args, int n, int64_t max_nt, cudaStream_t s);
+cudaError_t launch_boundary_post(const BoundaryArgs& a, cudaStream_t s);
 cudaError_t launch_gamma_star(const int32_t* n, const double* z, double* out, int64_t count, cudaStream_t s);
 cudaError_t launch_march_f64(const MarchArgs& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_tables32(const InstDesc& I, const cd* detab, const cd* rowscal, cudaStream_t s);

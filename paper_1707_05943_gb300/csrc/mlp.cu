@@ -27,7 +27,7 @@ namespace fdtd {
 
 __device__ int g_mlp_status;  // 1: an mbarrier wait of the GEMM ran out
 
-enum Epi { EPI_GELU = 0, EPI_LINEAR = 1, EPI_DGELU = 2, EPI_F32 = 3 };
+enum Epi { EPI_GELU = 0, EPI_LINEAR = 1, EPI_DGELU = 2, EPI_F32 = 3, EPI_ATOMIC = 4 };
 
 struct NtArgs {
   const __nv_bfloat16* A;  // [M][lda], K contiguous
@@ -40,6 +40,7 @@ struct NtArgs {
   __nv_bfloat16* out_bf16_t;  // optional transposed copy of out_bf16                     [N][ldt]
   const float* zprev;         // EPI_DGELU: [M][ldo]
   int ldo, ldt;
+  int kt_split;               // K slices per split (blockIdx.z); EPI_ATOMIC adds the partial sums
   long long spin;             // clock cycles an mbarrier wait may take before giving up
 };
 
@@ -128,7 +129,8 @@ __global__ void __launch_bounds__(128) k_gemm_nt_tc(const NtArgs g) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = tmem_sh;
-  const int nk = (g.K + TK - 1) / TK;
+  const int kt0 = blockIdx.z * g.kt_split;  // this split's first K slice
+  const int nk = min((g.K + TK - 1) / TK - kt0, g.kt_split);
 
   // one 128 x 64 slice of A and of B into stage s: 16-byte chunk q of a slice
   // is row r = (q & 7) + 8 (q >> 6), K-chunk c = (q >> 3) & 7, so that 8
@@ -136,7 +138,7 @@ __global__ void __launch_bounds__(128) k_gemm_nt_tc(const NtArgs g) {
   // row stay contiguous in global memory; rows >= M (N) and chunks >= K are zero
   auto load_slice = [&](int kt, int s) {
     const uint32_t sA = su32(sbase + (size_t)s * 2 * kTileBytes), sB = sA + kTileBytes;
-    const int k0 = kt * TK;
+    const int k0 = (kt0 + kt) * TK;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int q = tid + 128 * i;
@@ -221,6 +223,11 @@ __global__ void __launch_bounds__(128) k_gemm_nt_tc(const NtArgs g) {
       if (g.epi == EPI_GELU || g.epi == EPI_LINEAR) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) f[j] += __ldg(g.bias + nb + j);
+      }
+      if (g.epi == EPI_ATOMIC) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) atomicAdd(g.out_f32 + o + j, f[j]);
+        continue;
       }
       if (g.epi == EPI_GELU || g.epi == EPI_LINEAR || g.epi == EPI_F32) {
 #pragma unroll
@@ -330,6 +337,27 @@ __global__ void k_transpose_bf16(const __nv_bfloat16* in, __nv_bfloat16* out, in
     if (r < rows && c < cols) out[(size_t)c * rows + r] = t[threadIdx.x][i];
   }
 }
+// split-K finish of a data gradient: dz[b][k] = part[b][k] gelu'(z[b][k]) in BF16,
+// with its transpose, 32 x 32 tiles through shared memory
+__global__ void k_dgelu_finish(const float* part, const float* z, __nv_bfloat16* dz, __nv_bfloat16* dzt, int rows,
+                               int cols) {
+  __shared__ __nv_bfloat16 t[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) {
+      const size_t o = (size_t)r * cols + c;
+      const __nv_bfloat16 h = __float2bfloat16(part[o] * dgelu(z[o]));
+      dz[o] = h;
+      t[i][threadIdx.x] = h;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) dzt[(size_t)c * rows + r] = t[threadIdx.x][i];
+  }
+}
 // Adam on FP32 masters (Kingma & Ba, bias-corrected)
 __global__ void k_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2,
                        float eps, float c1, float c2) {
@@ -347,7 +375,18 @@ __global__ void k_to_bf16(const float* p, __nv_bfloat16* q, int64_t n) {
   if (i < n) q[i] = __float2bfloat16(p[i]);
 }
 
-static cudaError_t gemm_nt(NtArgs g, cudaStream_t s) {
+// K splits for a product with few output tiles and a long K (0 or 1: none)
+static int split_count(int M, int N, int K) {
+  const int tiles = ((M + TM - 1) / TM) * ((N + TN - 1) / TN);
+  const int kt = (K + TK - 1) / TK;
+  if (tiles >= 76 || kt < 16) return 1;
+  int sp = (152 + tiles - 1) / tiles;
+  if (sp > kt / 8) sp = kt / 8;  // at least 8 slices per split
+  return sp < 1 ? 1 : sp;
+}
+
+// launches the tiles of g; with splits > 1, g.epi must be EPI_ATOMIC into a zeroed FP32 C
+static cudaError_t gemm_nt(NtArgs g, cudaStream_t s, int splits = 1) {
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
@@ -355,7 +394,10 @@ static cudaError_t gemm_nt(NtArgs g, cudaStream_t s) {
   });
   if (attr != cudaSuccess) return attr;
   g.spin = 2000000000LL;  // about a second at the SM clock
-  dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM);
+  const int kt = (g.K + TK - 1) / TK;
+  g.kt_split = (kt + splits - 1) / splits;
+  splits = (kt + g.kt_split - 1) / g.kt_split;
+  dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM, splits);
   k_gemm_nt_tc<<<grid, 128, kGemmSmem, s>>>(g);
   return cudaGetLastError();
 }
@@ -408,6 +450,7 @@ struct Ws {
   __nv_bfloat16* dzt[2];
   float* dy32;
   __nv_bfloat16* wt;
+  float* part;  // split-K partial sums [batch][widest layer]
 };
 size_t ws_layout(const fdtd_mlp* d, int batch, char* base, Ws* w) {
   size_t off = 0;
@@ -435,6 +478,7 @@ size_t ws_layout(const fdtd_mlp* d, int batch, char* base, Ws* w) {
   }
   w->dy32 = (float*)take(sizeof(float) * (size_t)batch * d->dims[d->n_layers]);
   w->wt = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * maxW);
+  w->part = (float*)take(sizeof(float) * (size_t)batch * maxw);
   return off;
 }
 
@@ -575,13 +619,24 @@ fdtd_status fdtd_mlp_train_step(const fdtd_mlp* d, const float* x, const float* 
     gd.M = batch;
     gd.N = K;
     gd.K = N;
-    gd.epi = EPI_DGELU;
-    gd.zprev = w.z[l - 1];
-    gd.out_bf16 = w.dz[cur ^ 1];
-    gd.out_bf16_t = w.dzt[cur ^ 1];
     gd.ldo = K;
     gd.ldt = batch;
-    if (gemm_nt(gd, s) != cudaSuccess) return FDTD_ERR_CUDA;
+    const int sp = split_count(batch, K, N);
+    if (sp > 1) {
+      // long K over few tiles: partial sums in FP32, then GELU' and the casts
+      if (cudaMemsetAsync(w.part, 0, sizeof(float) * (size_t)batch * K, s) != cudaSuccess) return FDTD_ERR_CUDA;
+      gd.epi = EPI_ATOMIC;
+      gd.out_f32 = w.part;
+      if (gemm_nt(gd, s, sp) != cudaSuccess) return FDTD_ERR_CUDA;
+      k_dgelu_finish<<<dim3((K + 31) / 32, (batch + 31) / 32), dim3(32, 8), 0, s>>>(w.part, w.z[l - 1], w.dz[cur ^ 1],
+                                                                                    w.dzt[cur ^ 1], batch, K);
+    } else {
+      gd.epi = EPI_DGELU;
+      gd.zprev = w.z[l - 1];
+      gd.out_bf16 = w.dz[cur ^ 1];
+      gd.out_bf16_t = w.dzt[cur ^ 1];
+      if (gemm_nt(gd, s) != cudaSuccess) return FDTD_ERR_CUDA;
+    }
     cur ^= 1;
   }
   {
@@ -613,10 +668,17 @@ fdtd_status fdtd_gemm_bf16(const void* A, const void* B, float* C, int32_t M, in
   g.K = K;
   g.lda = lda;
   g.ldb = ldb;
-  g.epi = EPI_F32;
-  g.out_f32 = C;
   g.ldo = N;
-  return gemm_nt(g, (cudaStream_t)stream) == cudaSuccess ? FDTD_OK : FDTD_ERR_CUDA;
+  g.out_f32 = C;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int sp = split_count(M, N, K);
+  if (sp > 1) {
+    if (cudaMemsetAsync(C, 0, sizeof(float) * (size_t)M * N, s) != cudaSuccess) return FDTD_ERR_CUDA;
+    g.epi = EPI_ATOMIC;
+  } else {
+    g.epi = EPI_F32;
+  }
+  return gemm_nt(g, s, sp) == cudaSuccess ? FDTD_OK : FDTD_ERR_CUDA;
 }
 
 fdtd_status fdtd_mlp_status(void* stream) {
