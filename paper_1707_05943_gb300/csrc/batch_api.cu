@@ -42,10 +42,24 @@ fdtd_status cuda_fail(fdtd_plan_s* p, cudaError_t e, const char* where) {
 constexpr int kMidWeight = 16;
 
 // columns of CTA `rank` of `C`, as the kernel splits them (cost-weighted)
+// the device's column split (cta_range in march_f32c.cu), to size shared memory
 void cta_range_host(int64_t nx, int D, int rank, int C, int64_t* lo, int64_t* hi) {
   const int64_t G2 = std::min<int64_t>(2 * (int64_t)D, nx);
   const int64_t wm = kMidWeight;
   const int64_t W = wm * G2 + (nx - G2);
+  int64_t g = (2 * (int64_t)C * wm * G2 + W) / (2 * W);
+  if (g > C - 1) g = C - 1;
+  if (g >= 1 && nx > G2) {
+    if (rank < g) {
+      *lo = G2 * rank / g;
+      *hi = G2 * (rank + 1) / g;
+    } else {
+      const int64_t r = rank - g, Cb = C - g;
+      *lo = G2 + (nx - G2) * r / Cb;
+      *hi = G2 + (nx - G2) * (r + 1) / Cb;
+    }
+    return;
+  }
   auto inv = [&](int64_t x) { return x <= wm * G2 ? (x + wm - 1) / wm : G2 + (x - wm * G2); };
   *lo = inv(W * rank / C);
   *hi = inv(W * (rank + 1) / C);

@@ -13,11 +13,12 @@
 // at column m+1.  The boundary tables, the exact boundary value
 // psi(-a, t) at the first column and the norm reduction stay FP64.
 //
-// Work layout: thread-block clusters of up to 16 CTAs x 512 threads.  A
+// Work layout: thread-block clusters of up to 8 CTAs x 256 threads.  A
 // cluster takes the next work item from a queue (largest first): either one
-// wide instance, whose columns it splits over its CTAs (weighting the costlier
-// region -a < x <= 3a) and whose rows it marches with one cluster barrier per
-// row, or up to one narrow instance per CTA, marched with CTA barriers only.
+// wide instance, whose columns it splits over its CTAs (the costlier region
+// -a < x <= 3a on CTAs of its own when it is worth one, see cta_range) and
+// whose rows it marches with one cluster barrier per row, or up to one narrow
+// instance per CTA, marched with CTA barriers only.
 // Either way rows n-1, n-D and n-D-1 are complete when row n starts.  Inside a CTA each thread owns a contiguous
 // segment and runs the recurrence y_m = c2 y_{m-1} + r_m over it from a zero
 // carry; after a CTA barrier it takes its carry from the threads before it
@@ -193,11 +194,28 @@ __device__ __forceinline__ float ld_dsmem_f32(const float* local, unsigned rank)
   return v;
 }
 
-// columns of CTA `rank` of `C` for an instance: split by cost
+// columns of CTA `rank` of `C` for an instance.  The first G2 = 2D columns
+// (-a < x <= 3a) cost mid_weight bulk columns each.  When they are worth about
+// one CTA or more, whole CTAs take them (split evenly) and the others the bulk
+// (split evenly), so that no CTA mixes the two kinds; otherwise one cost-weighted
+// split.  The host mirrors this rule to size shared memory.
 __device__ __forceinline__ void cta_range(const InstDesc& I, int rank, int C, int64_t* lo, int64_t* hi) {
   const int64_t G2 = (2 * (int64_t)I.D < I.nx) ? 2 * (int64_t)I.D : I.nx;
   const int64_t wm = I.mid_weight;
   const int64_t W = wm * G2 + (I.nx - G2);
+  int64_t g = (2 * (int64_t)C * wm * G2 + W) / (2 * W);
+  if (g > C - 1) g = C - 1;
+  if (g >= 1 && I.nx > G2) {
+    if (rank < g) {
+      *lo = G2 * rank / g;
+      *hi = G2 * (rank + 1) / g;
+    } else {
+      const int64_t r = rank - g, Cb = C - g;
+      *lo = G2 + (I.nx - G2) * r / Cb;
+      *hi = G2 + (I.nx - G2) * (r + 1) / Cb;
+    }
+    return;
+  }
   auto inv = [&](int64_t x) { return x <= wm * G2 ? (x + wm - 1) / wm : G2 + (x - wm * G2); };
   *lo = inv(W * rank / C);
   *hi = inv(W * (rank + 1) / C);
@@ -371,6 +389,11 @@ __global__ void __launch_bounds__(kF32Threads, 1)
             t0 = c0 + (int64_t)tid * seg;
             if (t0 > c1) t0 = c1;
             t1 = (t0 + seg < c1) ? t0 + seg : c1;
+          } else if (len < kF32Threads) {
+            // fewer columns than threads: one column each on the first `len` threads, so
+            // that every carry in pass B crosses only non-empty segments
+            t0 = (tid < len) ? c0 + tid : c1;
+            t1 = (tid < len) ? t0 + 1 : c1;
           } else {
             t0 = c0 + len * tid / kF32Threads;
             t1 = c0 + len * (tid + 1) / kF32Threads;
@@ -562,14 +585,18 @@ __global__ void __launch_bounds__(kF32Threads, 1)
         if ((tid & 31) == 0) s_red[n & 1][tid >> 5] = nacc;
         if (solo) __syncthreads();
         else cluster_sync_all();
-        if (rank_e == 0 && tid == 0) {
-          double t = I.bnorm[n];
-          for (unsigned bb = 0; bb < C_e; ++bb)
-            for (int w = 0; w < kF32Threads / 32; ++w) {
-              const float* pw = &s_red[n & 1][w];
-              t += (double)(solo ? *pw : ld_dsmem_f32(pw, bb));
-            }
-          I.norms[n] = I.delta * t;
+        if (rank_e == 0 && tid < 32) {
+          // warp 0 of rank 0 gathers every warp's partial (local or over DSMEM) at once
+          constexpr int nw = kF32Threads / 32;
+          const int tot = (int)C_e * nw;
+          double t = 0.0;
+          for (int q = tid; q < tot; q += 32) {
+            const float* pw = &s_red[n & 1][q % nw];
+            t += (double)(solo ? *pw : ld_dsmem_f32(pw, (unsigned)(q / nw)));
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+          if (tid == 0) I.norms[n] = I.delta * (t + I.bnorm[n]);
         }
         slot = (slot + 1 == I.R) ? 0 : slot + 1;
         if (snap_ctr >= 0) snap_ctr = (snap_ctr == I.tstep) ? 0 : snap_ctr + 1;
