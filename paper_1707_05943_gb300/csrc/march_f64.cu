@@ -131,11 +131,12 @@ struct RowCtx {
   bool cold;        // first row of this launch: pair sums not yet in shared memory
 };
 
-// r_m for x > 3a (j >= 2D).
-__device__ __forceinline__ cd rhs_bulk(const MarchArgs& A, const RowCtx& R, int64_t j) {
+// r_m for x > 3a (j >= 2D), split as r_m = c2 b + q with b = psi[n-1][m]: the
+// recurrence step is then y_m = c2 (y_{m-1} + b) + q, one complex product fewer.
+__device__ __forceinline__ cd rhs_bulk_q(const MarchArgs& A, const RowCtx& R, int64_t j, cd& b) {
   const int D = A.D;
   cd r = A.c1 * ldring(R.row1 + j - 1);
-  r = cfma(A.c2, ldring(R.row1 + j), r);
+  b = ldring(R.row1 + j);
   if (R.rowD) {
     cd hn = ldring(R.rowD + j - D - 1) + ldring(R.rowD + j - D);  // row n-D pair
     if (R.rowD1) {
@@ -155,8 +156,22 @@ __device__ __forceinline__ cd rhs_bulk(const MarchArgs& A, const RowCtx& R, int6
 }
 
 __device__ __forceinline__ cd rhs_any(const MarchArgs& A, const RowCtx& R, int64_t j) {
-  if (j >= 2 * (int64_t)A.D) return rhs_bulk(A, R, j);
+  if (j >= 2 * (int64_t)A.D) {
+    cd b;
+    const cd q = rhs_bulk_q(A, R, j, b);
+    return cfma(A.c2, b, q);
+  }
   return rhs_general(A, R.n, R.nslot, j, R.R2);
+}
+
+// one step of the row recurrence at column j: y_j = c2 y_{j-1} + r_j
+__device__ __forceinline__ cd step_any(const MarchArgs& A, const RowCtx& R, int64_t j, cd y) {
+  if (j >= 2 * (int64_t)A.D) {
+    cd b;
+    const cd q = rhs_bulk_q(A, R, j, b);
+    return cfma(A.c2, y + b, q);
+  }
+  return cfma(A.c2, y, rhs_general(A, R.n, R.nslot, j, R.R2));
 }
 
 // store a final value of row n and add |y|^2 to the norm (the trapezoid's
@@ -272,11 +287,11 @@ __global__ void __launch_bounds__(kMarchThreads, 1) k_march_f64(const MarchArgs 
 #pragma unroll
     for (int v = 0; v < P; ++v) {
       const int64_t j = s0 + v;
-      if (j < s1) y = cfma(A.c2, y, rhs_any(A, R, j));
+      if (j < s1) y = step_any(A, R, j, y);
       y0[v] = y;
     }
     for (int64_t j = s0 + P; j < s1; ++j) {
-      y = cfma(A.c2, y, rhs_any(A, R, j));
+      y = step_any(A, R, j, y);
       if (j - s0 < A.kfix) stcg(R.row0 + j, y);  // provisional: receives the carry in pass B
       else finalize(R, j, y, nacc);
     }
