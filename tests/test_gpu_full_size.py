@@ -7,9 +7,9 @@ on outputs the oracle can compute.
   narrow box of the first D + 512 columns, which is exact there because a
   column only reads columns to its left and the exact boundary; every stored
   row must match it to 1e-12 relative L2.  Beyond the box, a property that
-  holds at any width: nothing reaches past the light cone of x = -a (on row
-  n, columns beyond n + 400 are exactly zero: the row recurrence's tail
-  |c2|^d underflows within ~110 columns at this delta).
+  holds at any width: nothing reaches past the light cone x = t + a of the
+  mirror source (on row n, columns beyond n + D + 400 are exactly zero: the
+  row recurrence's tail |c2|^d underflows well within 400 columns).
 * The seeded 256-instance complex64 batch (34 GB of rings, one plan, one
   persistent launch per 4096 rows): its three smallest instances against the
   oracle over every stored row, 1e-6 relative L2.
@@ -57,9 +57,10 @@ def test_large_fp64_prefix_full_width(F, oracle):
     assert np.all(np.isfinite(snaps))
     for i in range(snaps.shape[0]):
         n = i * (tstep + 1)
-        # ahead of the light cone of x = -a (column n on row n) the row recurrence leaves
-        # values of size |c2|^d at distance d, which underflow to zero within ~110 columns
-        assert not np.any(snaps[i, n + 400:]), n
+        # the sources reach x = t + a (line 3 of Eq. 1 switches on with theta(t - x + a)):
+        # column n + D - 1 on row n; ahead of it the row recurrence leaves values that
+        # shrink like |c2|^d with the distance d and underflow to zero well within 400 columns
+        assert not np.any(snaps[i, n + w.D + 400:]), n
 
 
 def test_seeded_batch_sampled_instances(F, oracle):
