@@ -174,6 +174,7 @@ def main():
     ap.add_argument("--workload", default="large", choices=["large", "small", "batch", "precision", "surrogate"])
     ap.add_argument("--batch-n", type=int, default=256, help="instances of the seeded batch")
     ap.add_argument("--compare-f64", action="store_true", help="also march the batch in FP64, one plan each")
+    ap.add_argument("--no-autotune", action="store_true", help="batch: default cluster width and split weight")
     ap.add_argument("--rows", type=int, default=0, help="march only this many rows (profiling)")
     ap.add_argument("--nx", type=int, default=0, help="march only this many columns (profiling)")
     ap.add_argument("--D", type=int, default=0, help="use this D at the same delta (profiling)")
@@ -363,12 +364,19 @@ def run_variant(args):
     ws_list = W.batch(n=args.batch_n) if args.workload == "batch" else [W.PRECISION]
     name = f"batch1707_n{len(ws_list)}" if args.workload == "batch" else W.PRECISION.name
 
-    def cfg(w, prec, tstep=-1):
+    def cfg(w, prec, tstep=-1, cluster_ctas=0, mid_weight=0):
         return F.Config(nx=w.nx, nt=w.nt, D=w.D, delta=w.delta, gamma=w.gamma, omega0=w.omega0, k=w.k,
                         init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center, tstep=tstep,
-                        precision=prec, rows_per_launch=0).c()
+                        precision=prec, rows_per_launch=0, cluster_ctas=cluster_ctas, mid_weight=mid_weight)
 
-    arr = (F.FdtdParams * len(ws_list))(*[cfg(w, F.F32_COMP) for w in ws_list])
+    knobs, tuned = {}, None
+    if args.workload == "batch" and not args.no_autotune:
+        from paper_1707_05943_gb300 import autotune as A
+        ch = A.tune([cfg(w, F.F32_COMP) for w in ws_list], rows=256)
+        knobs = {"cluster_ctas": ch.cluster_ctas, "mid_weight": ch.mid_weight}
+        tuned = {"cluster_ctas": ch.cluster_ctas, "mid_weight": ch.mid_weight, "key": ch.key,
+                 "estimated_march_ms": ch.table}
+    arr = (F.FdtdParams * len(ws_list))(*[cfg(w, F.F32_COMP, **knobs).c() for w in ws_list])
     nbytes, plan = ctypes.c_size_t(), ctypes.c_void_p()
     F._check(F.lib().fdtd_plan(arr, len(ws_list), None, ctypes.byref(nbytes), ctypes.byref(plan)), None, "plan")
     buf = torch.empty(nbytes.value + 256, dtype=torch.uint8, device="cuda")
@@ -383,7 +391,7 @@ def run_variant(args):
         e0.record(stream)
         F.fdtd_set_boundary(plan)
         e1.record(stream)
-        F.fdtd_march(plan, rows)
+        F.fdtd_march_graph(plan, rows)  # recorded on the first (warm-up) step, replayed after
         e2.record(stream)
         if record:
             ev.append((e0, e1, e2))
@@ -448,6 +456,8 @@ def run_variant(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "c64-compensated (FP64 boundary and norms)",
            "data": "synthetic",
            "config": {"workload": name, "instances": len(ws_list), "updates_per_step": updates,
+                      "march": "CUDA graph of the persistent launches (fdtd_march_graph)",
+                      "autotune": tuned,
                       "l2": "inputs larger than L2 (rings of all instances "
                             f"{sum((w.D + 2) * w.nx * 8 for w in ws_list) / 1e9:.1f} GB)"},
            "roofline": {"kernel": "k_march_f32c", "bound": "hbm", "achieved": ach, "peak": peaks.get("hbm_gbs"),

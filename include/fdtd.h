@@ -93,6 +93,10 @@ typedef struct {
   double center;         /* Gaussian centre x_c (IC 4); the pulse is cut at x=-a */
   int32_t tstep;         /* keep every (tstep+1)-th row as a snapshot; -1: none  */
   int32_t rows_per_launch; /* rows marched per kernel launch; 0 = default        */
+  int32_t cluster_ctas;  /* FDTD_F32_COMP: CTAs of the thread-block cluster that  */
+                         /* marches a wide instance, 1..8; 0 = by the widest one  */
+  int32_t mid_weight;    /* column split: cost of a column of -a < x <= 3a in     */
+                         /* bulk columns, 1..4096; 0 = 16                          */
 } fdtd_params;
 
 /* fdtd_set_boundary sources */
@@ -115,8 +119,8 @@ enum {
  *   p            : array of n_instances parameter sets (host memory, read only;
  *                  copied).  FDTD_F64 plans hold one instance.  FDTD_F32_COMP
  *                  plans hold 1 or more independent instances (each with its own
- *                  nx, nt, D, physics and tstep; rows_per_launch is taken from
- *                  p[0]); fdtd_march then advances every instance by n_rows in
+ *                  nx, nt, D, physics and tstep; rows_per_launch, cluster_ctas
+ *                  and mid_weight are taken from p[0]); fdtd_march then advances every instance by n_rows in
  *                  one persistent launch, a thread-block cluster per instance.
  *   cuda_stream  : cudaStream_t the plan queues its work on (NULL = default).
  *   workspace_bytes (out): device bytes the caller must lend (256-byte aligned).
@@ -154,6 +158,19 @@ fdtd_status fdtd_set_boundary(fdtd_plan_t plan, int32_t source, const void* devi
  * FDTD_ERR_CUDA.
  */
 fdtd_status fdtd_march(fdtd_plan_t plan, int64_t n_rows);
+
+/*
+ * fdtd_march_graph -- fdtd_march for FDTD_F32_COMP plans through a CUDA graph.
+ * The first call for a given (clamped) n_rows records the launch sequence of
+ * the march (descriptor advance, queue reset and one persistent launch per
+ * rows_per_launch rows) on an internal stream and instantiates it; later calls
+ * with the same n_rows replay it.  The replay is ordered after the work already
+ * queued on the plan's stream, and later work on that stream after it (events).
+ * The graph, the internal stream and its events are driver resources held by
+ * the plan until fdtd_destroy.  Results are bitwise those of fdtd_march.
+ * Errors: as fdtd_march, FDTD_ERR_UNSUPPORTED for FDTD_F64 plans.
+ */
+fdtd_status fdtd_march_graph(fdtd_plan_t plan, int64_t n_rows);
 
 /*
  * fdtd_readout -- synchronise the plan's stream and copy `kind` into dst.

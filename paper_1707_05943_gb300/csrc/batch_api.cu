@@ -43,9 +43,9 @@ constexpr int kMidWeight = 16;
 
 // columns of CTA `rank` of `C`, as the kernel splits them (cost-weighted)
 // the device's column split (cta_range in march_f32c.cu), to size shared memory
-void cta_range_host(int64_t nx, int D, int rank, int C, int64_t* lo, int64_t* hi) {
+void cta_range_host(int64_t nx, int D, int rank, int C, int wmid, int64_t* lo, int64_t* hi) {
   const int64_t G2 = std::min<int64_t>(2 * (int64_t)D, nx);
-  const int64_t wm = kMidWeight;
+  const int64_t wm = wmid;
   const int64_t W = wm * G2 + (nx - G2);
   int64_t g = (2 * (int64_t)C * wm * G2 + W) / (2 * W);
   if (g > C - 1) g = C - 1;
@@ -73,6 +73,7 @@ fdtd_status validate(const fdtd_params& p) {
   if (p.init_cond != FDTD_IC_TWO_PHOTON_GAUSS && !(p.alpha > 0)) return FDTD_ERR_INVALID_ARG;
   if (p.init_cond == FDTD_IC_TWO_PHOTON_GAUSS && !(p.sigma > 0)) return FDTD_ERR_INVALID_ARG;
   if (p.tstep < -1 || p.rows_per_launch < 0) return FDTD_ERR_INVALID_ARG;
+  if (p.cluster_ctas < 0 || p.cluster_ctas > 8 || p.mid_weight < 0 || p.mid_weight > 4096) return FDTD_ERR_INVALID_ARG;
   if (p.precision != FDTD_F32_COMP) return FDTD_ERR_INVALID_ARG;
   return FDTD_OK;
 }
@@ -103,7 +104,9 @@ fdtd_status batch_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n, v
   for (int i = 0; i < n; ++i) maxnx = std::max<int64_t>(maxnx, pin[i].nx);
   int cs = 1;
   while (cs < 8 && (int64_t)cs * fdtd::kF32Threads * 4 < maxnx) cs *= 2;
+  if (pin[0].cluster_ctas > 0) cs = pin[0].cluster_ctas;
   P->csize = cs;
+  P->mid_weight = pin[0].mid_weight > 0 ? pin[0].mid_weight : kMidWeight;
 
   size_t off = 0;
   P->off_sync = off;  off = align_up(off + sizeof(fdtd::SyncWords));
@@ -139,7 +142,7 @@ fdtd_status batch_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n, v
     int64_t cm = 0;
     for (int r = 0; r < cs; ++r) {
       int64_t lo, hi;
-      cta_range_host(p.nx, p.D, r, cs, &lo, &hi);
+      cta_range_host(p.nx, p.D, r, cs, P->mid_weight, &lo, &hi);
       cm = std::max(cm, hi - lo);
     }
     b.cols_max = cm + b.khalo;
@@ -258,7 +261,7 @@ fdtd_status batch_set_boundary(fdtd_plan_s* P, int32_t source, const void* table
     d.R = b.R;
     d.kfix = b.kfix;
     d.khalo = b.khalo;
-    d.mid_weight = kMidWeight;
+    d.mid_weight = P->mid_weight;
     d.tstep = p.tstep;
     auto f = [](cd v) { return make_float2((float)v.re, (float)v.im); };
     d.d1 = f(cd{b.c1.re - 1.0, b.c1.im});
@@ -344,6 +347,62 @@ fdtd_status batch_march(fdtd_plan_s* P, int64_t rows) {
                                   P->nclusters, P->csize, smem, s);
     if (e != cudaSuccess) return cuda_fail(P, e, "march_f32c launch");
   }
+  for (auto& b : P->inst) b.rows_done = std::min<int64_t>(b.p.nt, b.rows_done + rows);
+  P->rows_done = P->inst[0].rows_done;
+  return FDTD_OK;
+}
+
+// the same launches, recorded once per march length on an internal stream into a
+// CUDA graph and replayed behind an event on the plan's stream
+fdtd_status batch_march_graph(fdtd_plan_s* P, int64_t rows) {
+  int64_t maxleft = 0;
+  for (auto& b : P->inst) maxleft = std::max<int64_t>(maxleft, b.p.nt - b.rows_done);
+  if (rows > maxleft) rows = maxleft;
+  if (rows <= 0) return FDTD_OK;
+  const int n = (int)P->inst.size();
+  const int64_t per = P->p.rows_per_launch > 0 ? P->p.rows_per_launch : 4096;
+  cudaError_t e = cudaSuccess;
+  if (!P->cap_stream) {
+    e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(P, e, "graph stream/events");
+  }
+  if (!P->graph_exec || P->graph_rows != rows) {
+    if (P->graph_exec) {
+      cudaGraphExecDestroy(P->graph_exec);
+      P->graph_exec = nullptr;
+    }
+    cudaStream_t c = P->cap_stream;
+    const size_t smem = fdtd::march_f32c_smem(P->smem_cols);
+    e = cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(P, e, "cudaStreamBeginCapture");
+    for (int64_t done = 0; done < rows && e == cudaSuccess; done += per) {
+      const int64_t step = std::min<int64_t>(per, rows - done);
+      e = fdtd::launch_advance(at<fdtd::InstDesc>(P, P->off_desc), n, step, c);
+      if (e == cudaSuccess) e = cudaMemsetAsync(P->ws + P->off_queue, 0, sizeof(unsigned int), c);
+      if (e == cudaSuccess)
+        e = fdtd::launch_march_f32c(at<fdtd::InstDesc>(P, P->off_desc), at<fdtd::WorkItem>(P, P->off_order),
+                                    P->nitems, at<unsigned int>(P, P->off_queue), at<fdtd::SyncWords>(P, P->off_sync),
+                                    P->nclusters, P->csize, smem, c);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&P->graph_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      P->graph_exec = nullptr;
+      return cuda_fail(P, e, "graph capture");
+    }
+    P->graph_rows = rows;
+  }
+  e = cudaEventRecord(P->ev_in, P->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(P->cap_stream, P->ev_in, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(P->graph_exec, P->cap_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(P->ev_out, P->cap_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(P->stream, P->ev_out, 0);
+  if (e != cudaSuccess) return cuda_fail(P, e, "graph launch");
   for (auto& b : P->inst) b.rows_done = std::min<int64_t>(b.p.nt, b.rows_done + rows);
   P->rows_done = P->inst[0].rows_done;
   return FDTD_OK;

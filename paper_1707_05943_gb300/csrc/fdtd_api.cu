@@ -87,6 +87,7 @@ fdtd_status fdtd_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n_ins
   if (p.init_cond != FDTD_IC_TWO_PHOTON_GAUSS && !(p.alpha > 0)) return FDTD_ERR_INVALID_ARG;
   if (p.init_cond == FDTD_IC_TWO_PHOTON_GAUSS && !(p.sigma > 0)) return FDTD_ERR_INVALID_ARG;
   if (p.tstep < -1 || p.rows_per_launch < 0) return FDTD_ERR_INVALID_ARG;
+  if (p.cluster_ctas < 0 || p.cluster_ctas > 8 || p.mid_weight < 0 || p.mid_weight > 4096) return FDTD_ERR_INVALID_ARG;
   if (p.precision != FDTD_F64) return FDTD_ERR_UNSUPPORTED;
 
   P->p = p;
@@ -199,8 +200,8 @@ fdtd_status fdtd_set_boundary(fdtd_plan_t P, int32_t source, const void* device_
   }
   // column split: equal cost per CTA, with the region -a < x <= 3a (2D columns,
   // read through the general path) weighted kMidWeight
-  int kMidWeight = 16;  // measured: a column of -a < x <= 3a costs ~16 bulk columns
-  if (const char* w = getenv("FDTD_MID_WEIGHT")) kMidWeight = atoi(w) > 0 ? atoi(w) : kMidWeight;
+  // (measured: a column of -a < x <= 3a costs ~16 bulk columns in FP64)
+  const int kMidWeight = p.mid_weight > 0 ? p.mid_weight : 16;
   P->mid_weight = kMidWeight;
   int64_t split[fdtd::kMaxGrid + 1];
   {
@@ -252,6 +253,14 @@ fdtd_status fdtd_set_boundary(fdtd_plan_t P, int32_t source, const void* device_
   P->rows_done = 1;
   P->state = 2;
   return FDTD_OK;
+}
+
+fdtd_status fdtd_march_graph(fdtd_plan_t P, int64_t n_rows) {
+  if (!P) return FDTD_ERR_INVALID_ARG;
+  if (!P->batched) return fail(P, FDTD_ERR_UNSUPPORTED, "fdtd_march_graph needs an FDTD_F32_COMP plan");
+  if (P->state < 2) return fail(P, FDTD_ERR_STATE, "fdtd_march_graph before fdtd_set_boundary");
+  if (n_rows < 0) return fail(P, FDTD_ERR_INVALID_ARG, "n_rows < 0");
+  return batch_march_graph(P, n_rows);
 }
 
 fdtd_status fdtd_march(fdtd_plan_t P, int64_t n_rows) {

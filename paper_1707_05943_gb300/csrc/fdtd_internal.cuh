@@ -178,7 +178,18 @@ struct fdtd_plan_s {
   int nitems = 0;
   int csize = 0, nclusters = 0;
   int64_t smem_cols = 0;
+  // fdtd_march_graph: the recorded launch sequence of one march length
+  cudaGraphExec_t graph_exec = nullptr;
+  int64_t graph_rows = -1;
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   std::string last_error;
+  ~fdtd_plan_s() {
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+  }
 };
 
 // fills a plan without allocating it (fdtd_plan = new + this)
@@ -189,6 +200,7 @@ fdtd_status batch_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n, v
                             size_t* workspace_bytes);
 fdtd_status batch_set_boundary(fdtd_plan_s* P, int32_t source, const void* table, int64_t n);
 fdtd_status batch_march(fdtd_plan_s* P, int64_t rows);
+fdtd_status batch_march_graph(fdtd_plan_s* P, int64_t rows);
 int64_t batch_readout_bytes(fdtd_plan_s* P, int32_t inst, int32_t kind);
 fdtd_status batch_readout(fdtd_plan_s* P, int32_t inst, int32_t kind, void* dst, int64_t dst_bytes);
 

@@ -32,7 +32,7 @@ EXPORTS = ["fdtd_plan", "fdtd_bind_workspace", "fdtd_set_boundary", "fdtd_march"
            "fdtd_readout_bytes", "fdtd_destroy", "fdtd_status_string", "fdtd_last_error", "fdtd_gamma_star",
            "fdtd_march_noalloc", "fdtd_noalloc_max_bytes", "fdtd_readout_instance", "fdtd_readout_instance_bytes",
            "fdtd_mlp_param_count", "fdtd_mlp_workspace_bytes", "fdtd_mlp_sync_bf16", "fdtd_mlp_forward",
-           "fdtd_mlp_train_step", "fdtd_gemm_bf16", "fdtd_mlp_status"]
+           "fdtd_mlp_train_step", "fdtd_gemm_bf16", "fdtd_mlp_status", "fdtd_march_graph"]
 
 
 class FdtdParams(ctypes.Structure):
@@ -52,6 +52,8 @@ class FdtdParams(ctypes.Structure):
         ("center", ctypes.c_double),
         ("tstep", ctypes.c_int32),
         ("rows_per_launch", ctypes.c_int32),
+        ("cluster_ctas", ctypes.c_int32),
+        ("mid_weight", ctypes.c_int32),
     ]
 
 
@@ -89,6 +91,7 @@ def lib() -> ctypes.CDLL:
         L.fdtd_bind_workspace.argtypes = [vp, vp, sz]
         L.fdtd_set_boundary.argtypes = [vp, i32, vp, i64]
         L.fdtd_march.argtypes = [vp, i64]
+        L.fdtd_march_graph.argtypes = [vp, i64]
         L.fdtd_readout.argtypes = [vp, i32, vp, i64]
         L.fdtd_readout_bytes.argtypes = [vp, i32]
         L.fdtd_readout_bytes.restype = i64
@@ -116,7 +119,7 @@ def lib() -> ctypes.CDLL:
         for f in ("fdtd_plan", "fdtd_bind_workspace", "fdtd_set_boundary", "fdtd_march", "fdtd_readout",
                   "fdtd_gamma_star", "fdtd_march_noalloc", "fdtd_readout_instance", "fdtd_mlp_param_count",
                   "fdtd_mlp_workspace_bytes", "fdtd_mlp_sync_bf16", "fdtd_mlp_forward", "fdtd_mlp_train_step",
-                  "fdtd_gemm_bf16", "fdtd_mlp_status"):
+                  "fdtd_gemm_bf16", "fdtd_mlp_status", "fdtd_march_graph"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -155,6 +158,10 @@ def fdtd_set_boundary(plan, source: int = BOUNDARY_ANALYTIC, device_table: int =
 
 def fdtd_march(plan, n_rows: int):
     _check(lib().fdtd_march(plan, n_rows), plan, "fdtd_march")
+
+
+def fdtd_march_graph(plan, n_rows: int):
+    _check(lib().fdtd_march_graph(plan, n_rows), plan, "fdtd_march_graph")
 
 
 def fdtd_readout(plan, kind: int, dst_ptr: int, dst_bytes: int):
@@ -251,6 +258,8 @@ class Config:
     precision: int = F64
     tstep: int = -1
     rows_per_launch: int = 0
+    cluster_ctas: int = 0
+    mid_weight: int = 0
 
     def c(self) -> FdtdParams:
         p = FdtdParams()

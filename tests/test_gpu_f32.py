@@ -29,17 +29,18 @@ def oparams(O, w):
                     init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center)
 
 
-def cparams(F, w, tstep=0, rpl=0):
+def cparams(F, w, tstep=0, rpl=0, **kw):
     return F.Config(nx=w.nx, nt=w.nt, D=w.D, delta=w.delta, gamma=w.gamma, omega0=w.omega0, k=w.k,
                     init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center, tstep=tstep,
-                    precision=F.F32_COMP, rows_per_launch=rpl).c()
+                    precision=F.F32_COMP, rows_per_launch=rpl, **kw).c()
 
 
-def run_batch(F, ws, pieces=None, rpl=0):
-    """March a list of workloads as one complex64 plan; returns per-instance snapshots and norms."""
+def run_batch(F, ws, pieces=None, rpl=0, graph=False, repeat=1, **kw):
+    """March a list of workloads as one complex64 plan (through a CUDA graph when
+    `graph`; `repeat` times from the boundary); returns per-instance snapshots and norms."""
     import ctypes
     import torch
-    arr = (F.FdtdParams * len(ws))(*[cparams(F, w, rpl=rpl) for w in ws])
+    arr = (F.FdtdParams * len(ws))(*[cparams(F, w, rpl=rpl, **kw) for w in ws])
     L = F.lib()
     ws_bytes = ctypes.c_size_t()
     plan = ctypes.c_void_p()
@@ -48,9 +49,10 @@ def run_batch(F, ws, pieces=None, rpl=0):
     ws_t = torch.empty(ws_bytes.value + 256, dtype=torch.uint8, device="cuda")
     base = (ws_t.data_ptr() + 255) // 256 * 256
     F.fdtd_bind_workspace(plan, base, ws_bytes.value)
-    F.fdtd_set_boundary(plan)
-    for n in (pieces or [max(w.nt for w in ws)]):
-        F.fdtd_march(plan, n)
+    for _ in range(repeat):
+        F.fdtd_set_boundary(plan)
+        for n in (pieces or [max(w.nt for w in ws)]):
+            (F.fdtd_march_graph if graph else F.fdtd_march)(plan, n)
     out = []
     for i, w in enumerate(ws):
         snaps = np.empty(F.fdtd_readout_instance_bytes(plan, i, F.READ_SNAPSHOTS) // 8, dtype=np.complex64)
@@ -101,3 +103,44 @@ def test_pieces_and_launch_size_are_bitwise_equal(F):
     for a, b, c in zip(one, pieces, small):
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[0], c[0])
         assert np.array_equal(a[1], b[1]) and np.array_equal(a[1], c[1])
+
+
+def test_graph_replay_is_bitwise_equal(F):
+    ws = [W.exp_pair(900, 700, D=20), W.gauss_pair(2100, 500, D=40, a=1.0, gamma=1.0, k0a=0.7, sigma=1.5)]
+    plain = run_batch(F, ws, rpl=128)
+    graph = run_batch(F, ws, rpl=128, graph=True, repeat=2)      # recorded once, replayed
+    pieces = run_batch(F, ws, rpl=128, graph=True, pieces=[100, 100, 600])  # two lengths
+    for a, b, c in zip(plain, graph, pieces):
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        assert np.array_equal(a[0], c[0]) and np.array_equal(a[1], c[1])
+
+
+def test_graph_march_refuses_fp64_plans(F):
+    w = W.exp_pair(256, 64, D=8)
+    plan, nb = F.fdtd_plan(F.Config(nx=w.nx, nt=w.nt, D=w.D, delta=w.delta, gamma=w.gamma, omega0=w.omega0,
+                                    k=w.k, init_cond=w.init_cond).c())
+    try:
+        assert F.lib().fdtd_march_graph(plan, 10) == F.ERR_UNSUPPORTED
+    finally:
+        F.fdtd_destroy(plan)
+
+
+def test_autotune_and_plan_knobs(F, oracle, tmp_path):
+    # every cluster width and split weight marches the same solution (to FP32 rounding);
+    # the autotuner's choice is one of them
+    from paper_1707_05943_gb300 import autotune as A
+    ws = [W.gauss_pair(6000, 700, D=60, a=1.5, gamma=1.0, k0a=1.1, sigma=0.8),
+          W.gauss_pair(5000, 600, D=400, a=4.0, gamma=1.0, k0a=0.4, sigma=2.0),
+          W.exp_pair(700, 700, D=20), W.exp_pair(900, 500, D=12)]
+    refs = [oracle.march(oparams(oracle, w), tstep=0) for w in ws]
+    for cl, wt in ((1, 16), (2, 4), (8, 64)):
+        res = run_batch(F, ws, cluster_ctas=cl, mid_weight=wt)
+        for w, (snaps, norms), r in zip(ws, res, refs):
+            err = rel_l2(snaps, r["snaps"])
+            assert err < 1e-6, (cl, wt, w.name, err)
+    cfgs = [F.Config(nx=w.nx, nt=w.nt, D=w.D, delta=w.delta, gamma=w.gamma, omega0=w.omega0, k=w.k,
+                     init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center) for w in ws]
+    cand = ((2, 16), (4, 16), (8, 8), (8, 32))
+    ch = A.tune(cfgs, rows=128, candidates=cand, cache_path=str(tmp_path / "tune.json"))
+    print("autotune table (cluster CTAs, mid weight, ms):", ch.table)
+    assert (ch.cluster_ctas, ch.mid_weight) in cand and all(t[2] > 0 for t in ch.table)
