@@ -155,17 +155,38 @@ __device__ cd h_gauss(const BoundaryArgs& A, double tau, int panels) {
     if (lb + lnorm + log(hi - lo + 1e-300) < -41.5) continue;
     cd F = cd{0.0, 0.0};
     double h = (hi - lo) / panels;
-    for (int q = 0; q < panels; ++q) {
-      double c0 = lo + (q + 0.5) * h;
-      for (int i = 0; i < kGL; ++i) {
-        double v = c0 + 0.5 * h * c_gl_x[i];
-        double s = u - v;
-        if (j > 0 && s <= 0.0) continue;
-        double x = -a - v;
-        double re = j * lg2 - lgj - Wr * s - (x - A.center) * (x - A.center) / (4.0 * s2) + lnorm;
-        if (j > 0) re += j * log(s);
-        double im = -Wi * s + A.k * x;
-        F = F + (0.5 * h * c_gl_w[i]) * cexp_d(cd{re, im});
+    if (Wi == A.k) {
+      // resonant carrier: the phase -Wi s + k x = -Wi u - k a is the same at every
+      // node, so the quadrature sums a real integrand and takes the phase once
+      double Fr = 0.0;
+      for (int q = 0; q < panels; ++q) {
+        double c0 = lo + (q + 0.5) * h;
+        for (int i = 0; i < kGL; ++i) {
+          double v = c0 + 0.5 * h * c_gl_x[i];
+          double s = u - v;
+          if (j > 0 && s <= 0.0) continue;
+          double x = -a - v;
+          double re = j * lg2 - lgj - Wr * s - (x - A.center) * (x - A.center) / (4.0 * s2) + lnorm;
+          if (j > 0) re += j * log(s);
+          Fr += (0.5 * h * c_gl_w[i]) * exp(re);
+        }
+      }
+      double sn, cs;
+      sincos(-Wi * u - A.k * a, &sn, &cs);
+      F = cd{Fr * cs, Fr * sn};
+    } else {
+      for (int q = 0; q < panels; ++q) {
+        double c0 = lo + (q + 0.5) * h;
+        for (int i = 0; i < kGL; ++i) {
+          double v = c0 + 0.5 * h * c_gl_x[i];
+          double s = u - v;
+          if (j > 0 && s <= 0.0) continue;
+          double x = -a - v;
+          double re = j * lg2 - lgj - Wr * s - (x - A.center) * (x - A.center) / (4.0 * s2) + lnorm;
+          if (j > 0) re += j * log(s);
+          double im = -Wi * s + A.k * x;
+          F = F + (0.5 * h * c_gl_w[i]) * cexp_d(cd{re, im});
+        }
       }
     }
     tot = tot + F;
