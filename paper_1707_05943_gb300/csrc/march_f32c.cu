@@ -535,29 +535,21 @@ __global__ void __launch_bounds__(kF32Threads, 1)
             }
             const int nf = (I.kfix < (int)(t1 - t0)) ? I.kfix : (int)(t1 - t0);
             const int kb = (int)(t0 - c0), klast = (int)(I.nx - 1 - c0), kend = (int)(t1 - 1 - c0);
-            float2 Sq[kF32MaxTrunc], Aq[kF32MaxTrunc];
-#pragma unroll
-            for (int u = 0; u < kF32MaxTrunc; ++u) {
-              const int k = kb + (u < nf ? u : nf - 1);
-              Sq[u] = oh[k];
-              Aq[u] = oe[k];
-            }
             float2 ylast = y;
-#pragma unroll
-            for (int u = 0; u < kF32MaxTrunc; ++u) {
-              if (u < nf) {
-                const int k = kb + u;
-                const float2 S = fmac(I.c2pow[u + 1], carry, Sq[u]);
-                float2 sv, e;
-                two_sum(Aq[u].x, S.x, sv.x, e.x);
-                two_sum(Aq[u].y, S.y, sv.y, e.y);
-                oh[k] = sv;
-                oe[k] = e;
-                const float wt = (k == klast) ? 0.5f : 1.0f;
-                nacc = fmaf(wt * sv.x, sv.x, nacc);
-                nacc = fmaf(wt * sv.y, sv.y, nacc);
-                if (k == kend) ylast = sv;
-              }
+#pragma unroll 4
+            for (int u = 0; u < nf; ++u) {  // only the kfix parked columns take the carry
+              const int k = kb + u;
+              const float2 S = fmac(I.c2pow[u + 1], carry, oh[k]);
+              const float2 A = oe[k];
+              float2 sv, e;
+              two_sum(A.x, S.x, sv.x, e.x);
+              two_sum(A.y, S.y, sv.y, e.y);
+              oh[k] = sv;
+              oe[k] = e;
+              const float wt = (k == klast) ? 0.5f : 1.0f;
+              nacc = fmaf(wt * sv.x, sv.x, nacc);
+              nacc = fmaf(wt * sv.y, sv.y, nacc);
+              if (k == kend) ylast = sv;
             }
             if (t1 == c1) s_carry = ylast;  // carry into the next block
             if (gen && snap)
