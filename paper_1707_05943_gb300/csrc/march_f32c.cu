@@ -280,7 +280,8 @@ __global__ void __launch_bounds__(kF32Threads, 1)
   extern __shared__ __align__(128) float2 smem[];
   __shared__ float2 s_last[kF32Threads];
   __shared__ int s_len[kF32Threads];
-  __shared__ float2 s_carry;
+  __shared__ float2 s_carry[2];  // carry into a block, by block parity: a block's pass B reads one slot
+                                 // while the thread ending that block writes the other
   __shared__ float2 s_halo[kMaxTrunc];
   __shared__ float s_red[2][kF32Threads / 32];
   __shared__ int s_inst;
@@ -371,12 +372,42 @@ __global__ void __launch_bounds__(kF32Threads, 1)
           if (tid == 0) {
             float2 yh = (h0 == 0) ? I.bnd32[2 * n] : f2(0.f, 0.f);
             for (int c = 0; c < nh; ++c) yh = fmac(I.c2, yh, s_halo[c]);
-            s_carry = yh;
+            s_carry[0] = yh;
           }
         }
 
         // blocks: first the columns of -a < x <= 3a (read in place, cost-weighted
         // over the threads), then x > 3a in staged blocks of kBlk
+        // the six staged slices of a bulk block [b0, b1): rows n-1, n-D, n-D-1, the
+        // remainders of row n-1, and the source tables; thread 0 arms the barrier
+        // with their bytes and issues the copies
+        auto stage = [&](int64_t b0, int64_t b1, Slice& A1, Slice& AD, Slice& AD1, Slice& LO, Slice& DE,
+                         Slice& PH) {
+          const int64_t ib = n - b1 + D;  // detab index of the block's last column
+          const int64_t ilo = (ib > 0) ? ib : 0, ihi = n - b0 + D;        // detab [ilo, ihi)
+          const int64_t plo = (ib - D > 0) ? ib - D : 0, phi_ = n - b0;  // phitab [plo, phi_)
+          Copy cp[6];
+          cp[0] = plan_copy(A1, st_a1, R.row1, b0 - 1, b1);
+          cp[1] = R.rowD ? plan_copy(AD, st_ad, R.rowD, b0 - D - 1, b1 - D) : Copy{nullptr, nullptr, 0u};
+          cp[2] = (R.rowD1 && (!hs || R.cold)) ? plan_copy(AD1, st_ad1, R.rowD1, b0 - D - 1, b1 - D)
+                                               : Copy{nullptr, nullptr, 0u};
+          cp[3] = plan_copy(LO, st_lo, es_rd, b0, b1);
+          cp[4] = (ihi > ilo) ? plan_copy(DE, st_de, I.detab32, ilo, ihi) : Copy{nullptr, nullptr, 0u};
+          cp[5] = (phi_ > plo) ? plan_copy(PH, st_ph, I.phitab32, plo, phi_) : Copy{nullptr, nullptr, 0u};
+          if (tid == 0) {
+            unsigned bytes = 0;
+            for (int k = 0; k < 6; ++k) bytes += cp[k].bytes;
+            asm volatile("fence.proxy.async;\n" ::: "memory");
+            mbar_expect_tx(&s_bar, bytes);
+            for (int k = 0; k < 6; ++k)
+              if (cp[k].bytes) tma_load_1d(cp[k].dst, cp[k].src, cp[k].bytes, &s_bar);
+          }
+        };
+        // a bulk block's copies may be issued while the block before it finishes
+        // (pass B and the stores read only the output buffers)
+        bool pre = false;
+        Slice pA1, pAD, pAD1, pLO, pDE, pPH;
+        int blk = 0;  // block index within the row (selects the carry slot)
         int64_t c0 = j_lo;
         while (c0 < j_hi) {
           const bool gen = (c0 < G2);
@@ -401,27 +432,17 @@ __global__ void __launch_bounds__(kF32Threads, 1)
           s_len[tid] = (int)(t1 - t0);
 
           Slice A1, AD, AD1, LO, DE, PH;
-          const int64_t ib = n - c1 + D;  // detab index of the block's last column
           if (!gen) {
-            // stage the block's inputs: every thread plans the same six slices;
-            // thread 0 arms the barrier with their bytes and issues the copies
-            const int64_t ilo = (ib > 0) ? ib : 0, ihi = n - c0 + D;        // detab [ilo, ihi)
-            const int64_t plo = (ib - D > 0) ? ib - D : 0, phi_ = n - c0;  // phitab [plo, phi_)
-            Copy cp[6];
-            cp[0] = plan_copy(A1, st_a1, R.row1, c0 - 1, c1);
-            cp[1] = R.rowD ? plan_copy(AD, st_ad, R.rowD, c0 - D - 1, c1 - D) : Copy{nullptr, nullptr, 0u};
-            cp[2] = (R.rowD1 && (!hs || R.cold)) ? plan_copy(AD1, st_ad1, R.rowD1, c0 - D - 1, c1 - D)
-                                                 : Copy{nullptr, nullptr, 0u};
-            cp[3] = plan_copy(LO, st_lo, es_rd, c0, c1);
-            cp[4] = (ihi > ilo) ? plan_copy(DE, st_de, I.detab32, ilo, ihi) : Copy{nullptr, nullptr, 0u};
-            cp[5] = (phi_ > plo) ? plan_copy(PH, st_ph, I.phitab32, plo, phi_) : Copy{nullptr, nullptr, 0u};
-            if (tid == 0) {
-              unsigned bytes = 0;
-              for (int k = 0; k < 6; ++k) bytes += cp[k].bytes;
-              asm volatile("fence.proxy.async;\n" ::: "memory");
-              mbar_expect_tx(&s_bar, bytes);
-              for (int k = 0; k < 6; ++k)
-                if (cp[k].bytes) tma_load_1d(cp[k].dst, cp[k].src, cp[k].bytes, &s_bar);
+            if (pre) {
+              A1 = pA1;
+              AD = pAD;
+              AD1 = pAD1;
+              LO = pLO;
+              DE = pDE;
+              PH = pPH;
+              pre = false;
+            } else {
+              stage(c0, c1, A1, AD, AD1, LO, DE, PH);
             }
             // bounded wait for the copies
             long long tw = clock64();
@@ -519,6 +540,11 @@ __global__ void __launch_bounds__(kF32Threads, 1)
           }
           s_last[tid] = (t0 < t1) ? y : f2(0.f, 0.f);
           __syncthreads();
+          // the staging slices are free: issue the next bulk block's copies now
+          if (!gen && c1 < j_hi) {
+            stage(c1, (c1 + kBlk < j_hi) ? c1 + kBlk : j_hi, pA1, pAD, pAD1, pLO, pDE, pPH);
+            pre = true;
+          }
 
           // pass B: carry from the threads before (the block's carry-in for thread 0)
           if (t0 < t1) {
@@ -530,7 +556,7 @@ __global__ void __launch_bounds__(kF32Threads, 1)
                 ap = mulc(ap, (lu <= kF32MaxTrunc) ? I.c2pow[lu] : f2(0.f, 0.f));
                 if (ap.x * ap.x + ap.y * ap.y < 2.2e-16f) break;  // (2^-26)^2
               } else {
-                carry = fmac(ap, s_carry, carry);
+                carry = fmac(ap, s_carry[blk & 1], carry);
               }
             }
             const int nf = (I.kfix < (int)(t1 - t0)) ? I.kfix : (int)(t1 - t0);
@@ -551,7 +577,7 @@ __global__ void __launch_bounds__(kF32Threads, 1)
               nacc = fmaf(wt * sv.y, sv.y, nacc);
               if (k == kend) ylast = sv;
             }
-            if (t1 == c1) s_carry = ylast;  // carry into the next block
+            if (t1 == c1) s_carry[(blk + 1) & 1] = ylast;  // carry into the next block
             if (gen && snap)
               for (int64_t jj = t0; jj < t1; ++jj) snap[jj] = row0[jj];
           }
@@ -569,6 +595,7 @@ __global__ void __launch_bounds__(kF32Threads, 1)
             __syncthreads();  // staging and output buffers free for the next block
           }
           c0 = c1;
+          ++blk;
         }
 
         // norm: FP32 within a warp, FP64 across warps and CTAs
