@@ -6,7 +6,7 @@ on held-out parameters, with the march as the fallback.
 
 Sizes: 20480 training runs, 1024 calibration runs and 512 held-out runs of
 the surrogate grid (1024 x 1024, delta = 0.05), four networks 4 -> 512 x 4 ->
-512 trained for 30000 Adam steps of 512 samples each (about a minute in all).
+512 trained for 60000 Adam steps of 512 samples each (about a minute in all).
 """
 import numpy as np
 import pytest
@@ -45,7 +45,7 @@ def data(env):
 def trained(env, data):
     torch, S = env
     sur = S.Surrogate(K=4, outputs="norm", ranges=W.SURR_RANGES)
-    log = sur.fit(S.normalise(data["ftr"], W.SURR_RANGES), data["Ytr"], steps=30000, batch=512, lr=2e-3)
+    log = sur.fit(S.normalise(data["ftr"], W.SURR_RANGES), data["Ytr"], steps=60000, batch=512, lr=2e-3)
     print(f"training: {log.steps} steps x 4 networks in {log.seconds:.1f} s, final losses {log.final_loss}")
     q = sur.calibrate(S.normalise(data["fca"], W.SURR_RANGES), data["Yca"])
     print(f"calibration factor of the ensemble spread: {q:.3f}")
