@@ -13,6 +13,13 @@ N > 1 runs N independent replicas (one per rank, launched by torchrun); the
 value is the updates of all ranks over the slowest rank's time.  The
 reference arm (--impl reference) times the CPU oracle on a bounded sample of
 the same workload.
+
+Other workloads, one JSON line each:
+  --workload small      the 1024 x 4096 FP64 parity instance
+  --workload precision  8192 x 32768, complex64 compensated, error vs FP64 stated
+  --workload batch      256 seeded instances in one complex64 plan: autotuned
+                        knobs, CUDA-graph march, error vs FP64 stated
+  --workload surrogate  training and inference throughput of the surrogate network
 """
 from __future__ import annotations
 
@@ -339,10 +346,6 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
-
-
-def _clock_ok(clocks):
-    return clocks
 
 
 def run_variant(args):
