@@ -30,7 +30,7 @@ from dataclasses import dataclass
 
 from . import fdtd as F
 
-CANDIDATES = tuple((c, w) for c in (2, 4, 8) for w in (8, 16, 32))
+CANDIDATES = tuple((c, w) for c in (2, 4, 8) for w in (4, 8, 16, 32))
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 
