@@ -516,7 +516,7 @@ def run_surrogate(args, peaks, src):
            "config": {"workload": "surrogate_4x512x4_8704", "batch": batch,
                       "l2": "weights and activations L2-resident (training step; no flush)"},
            "inference": {"value": batch / (ms_inf * 1e-3), "unit": "samples/s", "ms_per_batch": ms_inf},
-           "roofline": {"kernel": "k_gemm_nt_tc (all GEMMs of the step)", "bound": "tensor", "achieved": ach,
+           "roofline": {"kernel": "k_gemm_nt_tma (all GEMMs of the step)", "bound": "tensor", "achieved": ach,
                         "peak": peaks.get("bf16_tflops"), "unit": "TFLOP/s",
                         "frac": ach / peaks.get("bf16_tflops", 1900.0), "traffic": None, "peak_source": src},
            "clocks": clocks}

@@ -314,8 +314,8 @@ fdtd_status fdtd_mlp_train_step(const fdtd_mlp* net, const float* x, const float
 /* The surrogate's GEMM on its own: C[M][N] (FP32, row-major, device) =
  * sum_k A[m lda + k] B[n ldb + k], A and B BF16 device arrays with K
  * contiguous (16-byte aligned, lda and ldb multiples of 8, >= K).  M, N
- * multiples of 64, K a multiple of 32.  Runs on the tensor cores (tcgen05,
- * FP32 accumulation in tensor memory). */
+ * multiples of 64, K a multiple of 32.  Runs on the tensor cores (operands
+ * staged by TMA, tcgen05 MMA, FP32 accumulation in tensor memory). */
 fdtd_status fdtd_gemm_bf16(const void* A, const void* B, float* C, int32_t M, int32_t N, int32_t K, int32_t lda,
                            int32_t ldb, void* cuda_stream);
 

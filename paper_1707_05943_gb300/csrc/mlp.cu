@@ -4,18 +4,18 @@
 //
 // GEMMs run on the fifth-generation tensor cores: every product is cast as
 // C[m][n] = sum_k A[m][k] B[n][k] with both operands K-contiguous BF16 in
-// global memory.  A CTA owns a 128 x 128 tile of C; cp.async stages 128 x 64
-// slices of A and B into shared memory (three stages) in the canonical
-// K-major core-matrix layout (8 rows x 16 bytes per core matrix, no swizzle);
-// one thread issues tcgen05.mma kind::f16 (M 128, N 128, K 16 per
-// instruction) into an FP32 accumulator in tensor memory and commits each
-// stage to an mbarrier; the epilogue reads the accumulator back with
-// tcgen05.ld (thread = row) and fuses bias, GELU, GELU' and the BF16 casts,
-// writing transposed copies where backpropagation needs the other operand
-// order.  Layer 0 (a handful of inputs) and the element-wise steps run on the
-// CUDA cores.
+// global memory.  A CTA owns a 128 x 128 tile of C; TMA copies 128 x 64
+// slices of A and B (three stages, 128-byte swizzle) into shared memory; one
+// thread issues tcgen05.mma kind::f16 (M 128, N 128, K 16 per instruction)
+// into an FP32 accumulator in tensor memory, with full/empty mbarriers per
+// stage; the epilogue reads the accumulator back with tcgen05.ld (thread =
+// row) and fuses bias, GELU, GELU' and the BF16 casts, writing transposed
+// copies where backpropagation needs the other operand order.  Layer 0 (a
+// handful of inputs) and the element-wise steps run on the CUDA cores.
+#include <cuda.h>  // CUtensorMap and its enums (types only; the encoder comes from the runtime)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <math.h>
 #include <stdint.h>
 
@@ -49,35 +49,17 @@ __device__ __forceinline__ float dgelu(float z) {
   return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
 
-constexpr int TM = 128, TN = 128, TK = 64, NSTAGE = 3;
+constexpr int TM = 128, TN = 128, TK = 64;
 constexpr int kTileBytes = TM * TK * 2;                       // 16 KB per operand slice
-constexpr int kGemmSmem = NSTAGE * 2 * kTileBytes + 1024;     // + alignment slack
 constexpr uint32_t kTmemCols = TN;                            // FP32 accumulator columns
 // instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9,
 // 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at 24-28
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
                             ((uint32_t)(TM >> 4) << 24);
-// core-matrix strides of a staged slice: K-adjacent core matrices 128 B apart,
-// 8-row groups (TK / 8) * 128 B apart
-constexpr uint32_t kLBO = 128, kSBO = (TK / 8) * 128;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// shared-memory matrix descriptor: start, leading and stride byte offsets (>> 4),
-// descriptor version 1 at bits 46-47, no swizzle
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((kLBO >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((kSBO >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
-}
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
 __device__ __forceinline__ bool mbar_done(uint32_t a, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -105,9 +87,94 @@ __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, long long
         "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])                    \
       : "r"(taddr))
 
-__global__ void __launch_bounds__(128) k_gemm_nt_tc(const NtArgs g) {
+// epilogue: thread (warp w, lane l) owns row m0 + 32 w + l of the tile and reads its
+// accumulator row from tensor memory 32 columns at a time
+__device__ __forceinline__ void tc_epilogue(const NtArgs& g, uint32_t tmem, int m0, int n0, int warp, int lane) {
+  const int m = m0 + warp * 32 + lane;
+#pragma unroll 1
+  for (int cb = 0; cb < TN; cb += 32) {
+    uint32_t v[32];
+    TC_LD32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+    const int nb = n0 + cb;
+    if (nb >= g.N || m >= g.M) continue;
+    float f[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(v[j]);
+    const size_t o = (size_t)m * g.ldo + nb;
+    if (g.epi == EPI_GELU || g.epi == EPI_LINEAR) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) f[j] += __ldg(g.bias + nb + j);
+    }
+    if (g.epi == EPI_ATOMIC) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) atomicAdd(g.out_f32 + o + j, f[j]);
+      continue;
+    }
+    if (g.epi == EPI_GELU || g.epi == EPI_LINEAR || g.epi == EPI_F32) {
+#pragma unroll
+      for (int j = 0; j < 32; j += 4)
+        *reinterpret_cast<float4*>(g.out_f32 + o + j) = make_float4(f[j], f[j + 1], f[j + 2], f[j + 3]);
+    }
+    if (g.epi == EPI_GELU || g.epi == EPI_DGELU) {
+      if (g.epi == EPI_GELU) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) f[j] = gelu(f[j]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+          const float4 z = *reinterpret_cast<const float4*>(g.zprev + o + j);
+          f[j] *= dgelu(z.x);
+          f[j + 1] *= dgelu(z.y);
+          f[j + 2] *= dgelu(z.z);
+          f[j + 3] *= dgelu(z.w);
+        }
+      }
+      __align__(16) __nv_bfloat16 h[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) h[j] = __float2bfloat16(f[j]);
+#pragma unroll
+      for (int j = 0; j < 32; j += 8)
+        *reinterpret_cast<uint4*>(g.out_bf16 + o + j) = *reinterpret_cast<const uint4*>(h + j);
+      if (g.out_bf16_t) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) g.out_bf16_t[(size_t)(nb + j) * g.ldt + m] = h[j];
+      }
+    }
+  }
+}
+
+// The product, with the operand slices staged by TMA: A and B are 2-D
+// tensor maps (K inner) with 128-byte swizzle, so that a 128 x 64 box lands in
+// shared memory in the K-major SWIZZLE_128B layout the MMA reads (8-row groups
+// 1024 B apart, each row's 128 B XOR-swizzled by the row index).  Thread 0 runs
+// the pipeline: it arms a stage's "full" mbarrier with the bytes of both boxes,
+// issues the two copies, and, when the stage is full, issues the four MMAs of
+// the slice and commits them to the stage's "empty" mbarrier, which it waits on
+// before reusing the stage.  Boxes past M, N or K are zero-filled by the copy.
+constexpr int kTmaStages = 3;
+constexpr int kGemmSmemTma = kTmaStages * 2 * kTileBytes + 1024;
+
+// shared-memory descriptor of a K-major SWIZZLE_128B operand: stride between
+// 8-row groups 1024 B, descriptor version 1, layout type 2 (128-byte swizzle);
+// the leading offset is unused for this layout
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::
+          "r"(dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(128) k_gemm_nt_tma(const NtArgs g, const __grid_constant__ CUtensorMap tmA,
+                                                     const __grid_constant__ CUtensorMap tmB) {
   extern __shared__ unsigned char dsmem[];
-  __shared__ __align__(8) uint64_t mbar[NSTAGE];
+  __shared__ __align__(8) uint64_t full[kTmaStages], empty[kTmaStages];
   __shared__ uint32_t tmem_sh;
   __shared__ int abort_sh;
   unsigned char* sbase = (unsigned char*)(((uintptr_t)dsmem + 1023) & ~(uintptr_t)1023);
@@ -121,7 +188,10 @@ __global__ void __launch_bounds__(128) k_gemm_nt_tc(const NtArgs g) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (tid == 0) {
-    for (int s = 0; s < NSTAGE; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&mbar[s])));
+    for (int s = 0; s < kTmaStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&empty[s])));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     abort_sh = 0;
   }
@@ -129,46 +199,35 @@ __global__ void __launch_bounds__(128) k_gemm_nt_tc(const NtArgs g) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = tmem_sh;
-  const int kt0 = blockIdx.z * g.kt_split;  // this split's first K slice
+  const int kt0 = blockIdx.z * g.kt_split;
   const int nk = min((g.K + TK - 1) / TK - kt0, g.kt_split);
 
-  // one 128 x 64 slice of A and of B into stage s: 16-byte chunk q of a slice
-  // is row r = (q & 7) + 8 (q >> 6), K-chunk c = (q >> 3) & 7, so that 8
-  // consecutive threads fill one core matrix (conflict-free) and 4 chunks of a
-  // row stay contiguous in global memory; rows >= M (N) and chunks >= K are zero
-  auto load_slice = [&](int kt, int s) {
-    const uint32_t sA = su32(sbase + (size_t)s * 2 * kTileBytes), sB = sA + kTileBytes;
-    const int k0 = (kt0 + kt) * TK;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int q = tid + 128 * i;
-      const int r = (q & 7) + 8 * (q >> 6), c = (q >> 3) & 7;
-      const uint32_t off = (uint32_t)(((r >> 3) * 8 + c) * 128 + (r & 7) * 16);
-      const int k = k0 + 8 * c;
-      const bool okA = (m0 + r) < g.M && k < g.K;
-      const bool okB = (n0 + r) < g.N && k < g.K;
-      cp_async16(sA + off, okA ? (const void*)(g.A + (size_t)(m0 + r) * g.lda + k) : (const void*)g.A, okA ? 16 : 0);
-      cp_async16(sB + off, okB ? (const void*)(g.B + (size_t)(n0 + r) * g.ldb + k) : (const void*)g.B, okB ? 16 : 0);
-    }
-  };
-
-  bool bad = false;
-#pragma unroll
-  for (int s = 0; s < NSTAGE - 1; ++s) {
-    if (s < nk) load_slice(s, s);
-    cp_async_commit();
-  }
-  for (int kt = 0; kt < nk; ++kt) {
-    const int s = kt % NSTAGE;
-    cp_async_wait<NSTAGE - 2>();
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
-    if (tid == 0 && !abort_sh) {
+  if (tid == 0) {
+    auto stage_a = [&](int kt) { return su32(sbase + (size_t)(kt % kTmaStages) * 2 * kTileBytes); };
+    auto issue = [&](int kt) {
+      const int s = kt % kTmaStages;
+      const uint32_t sA = stage_a(kt), sB = sA + kTileBytes;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(&full[s])),
+                   "r"(2 * kTileBytes)
+                   : "memory");
+      tma_2d(sA, &tmA, (kt0 + kt) * TK, m0, su32(&full[s]));
+      tma_2d(sB, &tmB, (kt0 + kt) * TK, n0, su32(&full[s]));
+    };
+    int issued = 0, kt = 0;
+    bool bad = false, lost_full = false;
+    for (; issued < nk && issued < kTmaStages; ++issued) issue(issued);
+    for (; kt < nk; ++kt) {
+      const int s = kt % kTmaStages;
+      const uint32_t ph = (uint32_t)((kt / kTmaStages) & 1);
+      if (!mbar_wait(su32(&full[s]), ph, g.spin)) {
+        bad = lost_full = true;
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint32_t sA = su32(sbase + (size_t)s * 2 * kTileBytes), sB = sA + kTileBytes;
+      const uint32_t sA = stage_a(kt), sB = sA + kTileBytes;
 #pragma unroll
       for (int kk = 0; kk < TK / 16; ++kk) {
-        const uint64_t da = sdesc(sA + kk * 256), db = sdesc(sB + kk * 256);
+        const uint64_t da = sdesc_sw128(sA + kk * 32), db = sdesc_sw128(sB + kk * 32);
         const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
         asm volatile(
             "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
@@ -177,90 +236,37 @@ __global__ void __launch_bounds__(128) k_gemm_nt_tc(const NtArgs g) {
             : "memory");
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                       su32(&mbar[s]))
+                       su32(&empty[s]))
                    : "memory");
-    }
-    // refill the stage of slice kt - 1 once its MMAs have read it
-    const int nt = kt + NSTAGE - 1;
-    if (nt < nk) {
-      const int sp = nt % NSTAGE;
-      const uint32_t par = (uint32_t)(((kt - 1) / NSTAGE) & 1);
-      if (kt >= 1 && !bad && !mbar_wait(su32(&mbar[sp]), par, g.spin)) {
-        bad = true;
-        atomicExch(&g_mlp_status, 1);
+      if (issued < nk) {  // issued == kt + kTmaStages: stage s is next, once the MMAs above have read it
+        if (!mbar_wait(su32(&empty[s]), ph, g.spin)) {
+          bad = true;
+          break;
+        }
+        issue(issued);
+        ++issued;
       }
-      if (!bad) load_slice(nt, sp);
     }
-    cp_async_commit();
-    if (bad) abort_sh = 1;  // read by the issuing thread after the next barrier
-  }
-  cp_async_wait<0>();
-  // the last commit covers every MMA of this CTA
-  if (!bad && nk > 0) {
-    const int s = (nk - 1) % NSTAGE;
-    if (!mbar_wait(su32(&mbar[s]), (uint32_t)(((nk - 1) / NSTAGE) & 1), g.spin)) {
-      bad = true;
+    if (bad) {
       atomicExch(&g_mlp_status, 1);
+      abort_sh = 1;
+      // let the copies still in flight land before the CTA leaves (bounded)
+      for (int k = lost_full ? kt : kt + 1; k < issued; ++k)
+        mbar_wait(su32(&full[k % kTmaStages]), (uint32_t)((k / kTmaStages) & 1), g.spin);
     }
   }
-  if (bad) abort_sh = 1;
+  __syncthreads();
+  if (!abort_sh) {
+    // the last commit covers every MMA of this CTA
+    const int s = (nk - 1) % kTmaStages;
+    if (!mbar_wait(su32(&empty[s]), (uint32_t)(((nk - 1) / kTmaStages) & 1), g.spin)) {
+      atomicExch(&g_mlp_status, 1);
+      abort_sh = 1;
+    }
+  }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-
-  if (!abort_sh) {
-    const int m = m0 + warp * 32 + lane;
-#pragma unroll 1
-    for (int cb = 0; cb < TN; cb += 32) {
-      uint32_t v[32];
-      TC_LD32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
-      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-      const int nb = n0 + cb;
-      if (nb >= g.N || m >= g.M) continue;
-      float f[32];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(v[j]);
-      const size_t o = (size_t)m * g.ldo + nb;
-      if (g.epi == EPI_GELU || g.epi == EPI_LINEAR) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) f[j] += __ldg(g.bias + nb + j);
-      }
-      if (g.epi == EPI_ATOMIC) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) atomicAdd(g.out_f32 + o + j, f[j]);
-        continue;
-      }
-      if (g.epi == EPI_GELU || g.epi == EPI_LINEAR || g.epi == EPI_F32) {
-#pragma unroll
-        for (int j = 0; j < 32; j += 4)
-          *reinterpret_cast<float4*>(g.out_f32 + o + j) = make_float4(f[j], f[j + 1], f[j + 2], f[j + 3]);
-      }
-      if (g.epi == EPI_GELU || g.epi == EPI_DGELU) {
-        if (g.epi == EPI_GELU) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) f[j] = gelu(f[j]);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; j += 4) {
-            const float4 z = *reinterpret_cast<const float4*>(g.zprev + o + j);
-            f[j] *= dgelu(z.x);
-            f[j + 1] *= dgelu(z.y);
-            f[j + 2] *= dgelu(z.z);
-            f[j + 3] *= dgelu(z.w);
-          }
-        }
-        __align__(16) __nv_bfloat16 h[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) h[j] = __float2bfloat16(f[j]);
-#pragma unroll
-        for (int j = 0; j < 32; j += 8)
-          *reinterpret_cast<uint4*>(g.out_bf16 + o + j) = *reinterpret_cast<const uint4*>(h + j);
-        if (g.out_bf16_t) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) g.out_bf16_t[(size_t)(nb + j) * g.ldt + m] = h[j];
-        }
-      }
-    }
-  }
+  if (!abort_sh) tc_epilogue(g, tmem, m0, n0, warp, lane);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
@@ -386,19 +392,48 @@ static int split_count(int M, int N, int K) {
 }
 
 // launches the tiles of g; with splits > 1, g.epi must be EPI_ATOMIC into a zeroed FP32 C
+// tensor map of a K-contiguous BF16 operand [rows][ld], boxes of 128 rows x 64 K,
+// 128-byte swizzle, zero fill outside
+static cudaError_t make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int K, int ld) {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  if (!enc) return cudaErrorNotSupported;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(__nv_bfloat16)};
+  const cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)TM};
+  const cuuint32_t es[2] = {1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides, box,
+                         es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// launches the tiles of g; with splits > 1, g.epi must be EPI_ATOMIC into a zeroed FP32 C
 static cudaError_t gemm_nt(NtArgs g, cudaStream_t s, int splits = 1) {
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(k_gemm_nt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+    attr = cudaFuncSetAttribute(k_gemm_nt_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmemTma);
   });
   if (attr != cudaSuccess) return attr;
   g.spin = 2000000000LL;  // about a second at the SM clock
   const int kt = (g.K + TK - 1) / TK;
   g.kt_split = (kt + splits - 1) / splits;
   splits = (kt + g.kt_split - 1) / g.kt_split;
+  alignas(64) CUtensorMap mA, mB;
+  cudaError_t e = make_map(&mA, g.A, g.M, g.K, g.lda);
+  if (e == cudaSuccess) e = make_map(&mB, g.B, g.N, g.K, g.ldb);
+  if (e != cudaSuccess) return e;
   dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM, splits);
-  k_gemm_nt_tc<<<grid, 128, kGemmSmem, s>>>(g);
+  k_gemm_nt_tma<<<grid, 128, kGemmSmemTma, s>>>(g, mA, mB);
   return cudaGetLastError();
 }
 
