@@ -556,7 +556,7 @@ cudaError_t forward(const fdtd_mlp* d, const float* x, int batch, const Ws& w, b
 }
 
 // BF16 weight blocks of layers >= 1 start where the FP32 ones do, so their byte
-// offsets are 2 * the float offsets: they must be 16-byte aligned for cp.async
+// offsets are 2 * the float offsets: they must be 16-byte aligned for the tensor maps
 bool weights_aligned(const fdtd_mlp* d) {
   int64_t offW[8], offb[8], total;
   layer_offsets(d, offW, offb, &total);
