@@ -27,6 +27,9 @@
  *                    as the boundary (Sec. 2, "boundary needs only x<-a").
  *   orc_march_left   the same update marched inside x <= -a (validation test 1
  *                    of Sec. 4), with an exact band to its left.
+ *   orc_measures     mu(t), lambda(t) and det M_t of the non-Markovian measure
+ *                    (App. D) from the march's snapshot rows and norms, with the
+ *                    one-excitation photon phi(x,t) (orc_phi1) and atom e0(t).
  *
  * Parity status of each function is stated in the test suite; the readings
  * taken where the paper is silent are listed in the design notes:
@@ -613,6 +616,110 @@ int orc_march_left(const orc_params* p, int64_t n_rows, int64_t L, double* grid)
   free(s.store);
   free(et);
   if (bad) return ORC_BAD_READ;
+  return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Non-Markovian measures, App. D (stimulated-emission class only).         */
+/* ------------------------------------------------------------------------ */
+
+/* theta with theta(0) = 1/2 (the reading used for the source gates). */
+static double theta_half_d(double v, double eps) { return v > eps ? 1.0 : (v < -eps ? 0.0 : 0.5); }
+
+/* phi(x,t): the photon of the one-excitation sector when the wavepacket phi0 of
+ * Sec. 2 (b) comes in and the atom starts in its ground state.  The paper uses
+ * it in mu(t) without printing it; it is the one-excitation analogue of the
+ * formal solution Eq. 2: the free packet minus what the atom at x = -a and its
+ * mirror image at x = +a emit,
+ *   phi(x,t) = phi0(x-t) - sqrt(Gamma/2) [ theta(x+a) theta(t-x-a) e0(t-x-a)
+ *                                          - theta(x-a) theta(t-x+a) e0(t-x+a) ],
+ * with e0 the atom amplitude of the same problem (Sec. 2 (c) formula, with the
+ * e^{-ika} factor).  Read at x = -a and x = +a the two gates give back the
+ * delay equation that e0 solves (the test suite pins this form by
+ * |e0|^2 + int |phi|^2 = 1). */
+static int phi1_at(const orc_params* p, double x, double t, cplx* out) {
+  double a = half_a(p), eps = 1e-9 * p->delta;
+  cplx v = phi_at(p, x - t), e = 0;
+  int st = ORC_OK;
+  double u2 = t - x - a, w2 = theta_half_d(x + a, eps) * theta_half_d(u2, eps);
+  if (w2 > 0.0 && (st = e0exp_at(p, u2 < 0 ? 0.0 : u2, &e)) != ORC_OK) return st;
+  v -= sqrt(0.5 * p->gamma) * w2 * e;
+  double u3 = t - x + a, w3 = theta_half_d(x - a, eps) * theta_half_d(u3, eps);
+  if (w3 > 0.0) {
+    if ((st = e0exp_at(p, u3 < 0 ? 0.0 : u3, &e)) != ORC_OK) return st;
+    v += sqrt(0.5 * p->gamma) * w3 * e;
+  }
+  *out = v;
+  return ORC_OK;
+}
+
+int orc_phi1(const orc_params* p, double x, double t, double* re, double* im) {
+  cplx v = 0;
+  int st = phi1_at(p, x, t, &v);
+  *re = creal(v);
+  *im = cimag(v);
+  return st;
+}
+
+/* e0(t) of the one-excitation sector (atom in its ground state, phi0 incident):
+ * the Sec. 2 (c) formula (App. D names it in lambda(t)). */
+int orc_e0_at(const orc_params* p, double t, double* re, double* im) {
+  cplx v = 0;
+  int st = (t < 0.0) ? ORC_OK : e0exp_at(p, t, &v);
+  *re = creal(v);
+  *im = cimag(v);
+  return st;
+}
+
+/*
+ * mu(t) = int phi*(x,t) psi(x,t) dx and lambda(t) = int |psi(x,t)|^2 dx - |e0(t)|^2
+ * (App. D), and det M_t = |mu|^2 lambda, on the snapshot rows of a march of the
+ * stimulated-emission class (init_cond 2): snaps[s] is row n = s (tstep+1),
+ * norms[n] the march's N(n) (trapezoid of |psi|^2 over [-a, x_last]).
+ * x <= -a is exact: psi = phi0(x-t) e1(t) and phi = phi0(x-t) there, and
+ * int_{-inf}^{-a} |phi0(x-t)|^2 dx = e^{-alpha Gamma t}, so
+ *   mu     = e1(t) e^{-alpha Gamma t} + trapezoid over [-a, x_last] of conj(phi) psi,
+ *   lambda = |e1(t)|^2 e^{-alpha Gamma t} + N(n) - |e0(t)|^2.
+ * The trapezoid's first node x = -a takes psi(-a,t) = phi0(-a-t) e1(t) and the
+ * right limit of phi (the emitted part switched on).  out: per snapshot row,
+ * (Re mu, Im mu, lambda, det M).
+ */
+int orc_measures(const orc_params* p, int64_t n_rows, int64_t tstep, const double* snaps, const double* norms,
+                 double* out) {
+  int st = check_params(p);
+  if (st != ORC_OK) return st;
+  if (p->init_cond != 2 || tstep < 0 || n_rows < 1) return ORC_BAD_ARG;
+  const double a = half_a(p), dl = p->delta, ag = p->alpha * p->gamma;
+  const int64_t Dh = p->D / 2, ns = (n_rows - 1) / (tstep + 1) + 1;
+  const cplx* sn = (const cplx*)snaps;
+  for (int64_t s = 0; s < ns; ++s) {
+    const int64_t n = s * (tstep + 1);
+    const double t = n * dl;
+    double er, ei, zr, zi;
+    int s1 = orc_e_at(p, t, &er, &ei);
+    int s2 = orc_e0_at(p, t, &zr, &zi);
+    if (s1 != ORC_OK) st = s1;
+    if (s2 != ORC_OK) st = s2;
+    const cplx e1 = CMPLX(er, ei), e0 = CMPLX(zr, zi);
+    /* first node x = -a: right limit of phi */
+    cplx phl = phi_at(p, -a - t) - sqrt(0.5 * p->gamma) * (n == 0 ? 0.5 : 1.0) * e0;
+    cplx acc = 0.5 * conj(phl) * (phi_at(p, -a - t) * e1);
+    for (int64_t j = 0; j < p->nx; ++j) {
+      const double x = (double)(j - Dh + 1) * dl;
+      cplx ph;
+      int s3 = phi1_at(p, x, t, &ph);
+      if (s3 != ORC_OK) st = s3;
+      const cplx v = conj(ph) * sn[s * p->nx + j];
+      acc += (j == p->nx - 1) ? 0.5 * v : v;
+    }
+    const double decay = exp(-ag * t);
+    const cplx mu = e1 * decay + dl * acc;
+    const double lam = creal(e1 * conj(e1)) * decay + norms[n] - creal(e0 * conj(e0));
+    out[4 * s] = creal(mu);
+    out[4 * s + 1] = cimag(mu);
+    out[4 * s + 2] = lam;
+    out[4 * s + 3] = creal(mu * conj(mu)) * lam;
+  }
   return st;
 }
 

@@ -70,8 +70,12 @@ def lib():
                                 ctypes.c_void_p, ctypes.c_void_p]
         L.orc_march_left.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
         L.orc_psi_exact.argtypes = [P, ctypes.c_int64, ctypes.c_int64, dp, dp]
+        L.orc_phi1.argtypes = [P, ctypes.c_double, ctypes.c_double, dp, dp]
+        L.orc_e0_at.argtypes = [P, ctypes.c_double, dp, dp]
+        L.orc_measures.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p]
         for f in (L.orc_G, L.orc_P, L.orc_phi, L.orc_e_at, L.orc_etable, L.orc_march, L.orc_march_left,
-                  L.orc_psi_exact):
+                  L.orc_psi_exact, L.orc_phi1, L.orc_e0_at, L.orc_measures):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -187,3 +191,31 @@ def march_left(p: Params, n_rows: int, L: int) -> np.ndarray:
     cp = p.c()
     _check(lib().orc_march_left(ctypes.byref(cp), int(n_rows), int(L), grid.ctypes.data), "orc_march_left")
     return grid
+
+
+def phi1(p: Params, x: float, t: float) -> complex:
+    """One-excitation photon field phi(x,t) (atom starting in its ground state)."""
+    re, im = ctypes.c_double(), ctypes.c_double()
+    cp = p.c()
+    _check(lib().orc_phi1(ctypes.byref(cp), float(x), float(t), ctypes.byref(re), ctypes.byref(im)), "orc_phi1")
+    return complex(re.value, im.value)
+
+
+def e0_one(p: Params, t: float) -> complex:
+    """e0(t) of the one-excitation sector (Sec. 2 (c) formula) for the photon of p."""
+    re, im = ctypes.c_double(), ctypes.c_double()
+    cp = p.c()
+    _check(lib().orc_e0_at(ctypes.byref(cp), float(t), ctypes.byref(re), ctypes.byref(im)), "orc_e0_at")
+    return complex(re.value, im.value)
+
+
+def measures(p: Params, march_out: dict, tstep: int) -> np.ndarray:
+    """(Re mu, Im mu, lambda, det M) per snapshot row of an init_cond-2 march (App. D)."""
+    snaps = np.ascontiguousarray(march_out["snaps"])
+    norms = np.ascontiguousarray(march_out["norms"])
+    n_rows = norms.shape[0]
+    out = np.zeros((snaps.shape[0], 4))
+    cp = p.c()
+    _check(lib().orc_measures(ctypes.byref(cp), n_rows, tstep, snaps.ctypes.data, norms.ctypes.data,
+                              out.ctypes.data), "orc_measures")
+    return out
