@@ -45,7 +45,12 @@ UNIT = "grid-point updates/s"
 #          + y_{m-1} + b (2) + c2 (y_{m-1} + b) (6+2) = 46
 BYTES_PER_UPDATE_F64 = 32
 FLOPS_PER_UPDATE_F64 = 46
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64 (vector and tensor), NVIDIA's figure
+# double-float march (k_march_dw), per bulk update: FP32-pipe instructions (FADD, FMUL, FFMA
+# each 1) and flops (FMA = 2), counted from its source: 5 complex double-float products of
+# the right-hand side, 3 sums, the recurrence step and renormalisation, the norm term, and
+# the carry correction on ~6 of every 15 columns
+DW_FP32_INSTR_PER_UPDATE = 376
+DW_FLOPS_PER_UPDATE = 460
 
 
 def env_rank():
@@ -186,6 +191,9 @@ def main():
     ap.add_argument("--nx", type=int, default=0, help="march only this many columns (profiling)")
     ap.add_argument("--D", type=int, default=0, help="use this D at the same delta (profiling)")
     ap.add_argument("--rows-per-launch", type=int, default=4096)
+    ap.add_argument("--mid-weight", type=int, default=0, help="column split weight of -a < x <= 3a (0: default)")
+    ap.add_argument("--precision", default="f64", choices=["f64", "dw"],
+                    help="large/small workloads: FP64 march or the double-float march (same parity bar)")
     ap.add_argument("--ref-rows", type=int, default=4096)
     ap.add_argument("--cpu-rows", type=int, default=6144)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -223,12 +231,15 @@ def main():
 
     stream = torch.cuda.Stream(device=dev)
     rpl = args.rows_per_launch
+    prec = fdtd.F64_DW if args.precision == "dw" else fdtd.F64
     cfg = fdtd.Config(nx=w.nx, nt=w.nt, D=w.D, delta=w.delta, gamma=w.gamma, omega0=w.omega0, k=w.k,
                       init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center, tstep=-1,
-                      rows_per_launch=rpl)
+                      rows_per_launch=rpl, precision=prec, mid_weight=args.mid_weight)
     solver = fdtd.Solver(cfg, stream=stream)
     # boundary: phi table, row scalars, e-table pass 1 (+ pass 2 for the two-photon classes), norm, detab
-    launches_per_step = (5 if w.init_cond == 2 else 6) + math.ceil((w.nt - 1) / rpl)
+    # (double-float: + the table split, and one norm reduction after every march launch)
+    chunks = math.ceil((w.nt - 1) / rpl)
+    launches_per_step = (5 if w.init_cond == 2 else 6) + (chunks if prec == fdtd.F64 else 1 + 2 * chunks)
 
     def step(events=None):
         solver.set_boundary()
@@ -258,6 +269,9 @@ def main():
         norms_w = solver.read(fdtd.READ_NORMS)
         assert np.all(np.isfinite(norms_w))
 
+    # measured arithmetic peaks of this GPU (the roofline denominators of the marches)
+    alu_peaks = {"fp64": fdtd.fdtd_alu_probe(0, stream.cuda_stream) / 1e12,
+                 "fp32": fdtd.fdtd_alu_probe(1, stream.cuda_stream) / 1e12}
     sampler = ClockSampler(local)
     events = []
     barrier()
@@ -279,34 +293,48 @@ def main():
 
     # dominant kernel: the march launches (full-size ones)
     full = [(a.elapsed_time(b), n) for a, b, n in events if n == rpl] or [(a.elapsed_time(b), n) for a, b, n in events]
-    # DRAM bytes per update from one ncu capture of k_march_f64 (2^20 columns, D = 100, 4096 rows:
-    # 137.9 GB per launch); the D = 2000 launch moves the same bytes per update (both delay rows
-    # lie far outside L2), so the figure is scaled by the updates of one launch
-    ncu_bytes_per_update = 32.1
     avg_ms = sum(t for t, _ in full) / len(full)
     rows_l = full[0][1]
     peaks, src = load_peaks()
     upd_launch = rows_l * w.nx
-    flops_launch = FLOPS_PER_UPDATE_F64 * upd_launch
-    bytes_launch = BYTES_PER_UPDATE_F64 * upd_launch
-    ach_tf = flops_launch / (avg_ms * 1e-3) / 1e12
-    ach_gbs = bytes_launch / (avg_ms * 1e-3) / 1e9
-    roof = {"kernel": "k_march_f64", "bound": "alu", "achieved": ach_tf, "peak": FP64_NOMINAL_TFLOPS,
-            "unit": "TFLOP/s", "frac": ach_tf / FP64_NOMINAL_TFLOPS,
-            "peak_source": "GB300 nominal dense FP64 1.25 TFLOP/s (no FP64 figure in MEASURED_PEAKS.json)",
-            "flops_per_update": FLOPS_PER_UPDATE_F64, "updates_per_launch": upd_launch,
-            "launch_ms": avg_ms, "traffic": ncu_bytes_per_update * upd_launch,
-            "traffic_source": "ncu dram__bytes_read+write of k_march_f64 at nx 2^20, D 100 (32.1 B/update), "
-                              "scaled to this launch's updates",
-            "hbm": {"achieved": ach_gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                    "frac": ach_gbs / peaks.get("hbm_gbs", 6800.0), "bytes_per_update": BYTES_PER_UPDATE_F64,
-                    "peak_source": src}}
+    ach_gbs = BYTES_PER_UPDATE_F64 * upd_launch / (avg_ms * 1e-3) / 1e9
+    hbm = {"achieved": ach_gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+           "frac": ach_gbs / peaks.get("hbm_gbs", 6800.0), "bytes_per_update": BYTES_PER_UPDATE_F64,
+           "peak_source": src}
+    if prec == fdtd.F64:
+        # DRAM bytes per update from one ncu capture of k_march_f64 (2^20 columns, D = 100, 4096 rows:
+        # 137.9 GB per launch); the D = 2000 launch moves the same bytes per update (both delay rows
+        # lie far outside L2), so the figure is scaled by the updates of one launch
+        ach = FLOPS_PER_UPDATE_F64 * upd_launch / (avg_ms * 1e-3) / 1e12
+        roof = {"kernel": "k_march_f64", "bound": "alu", "achieved": ach, "peak": alu_peaks["fp64"],
+                "unit": "TFLOP/s", "frac": ach / alu_peaks["fp64"],
+                "peak_source": "measured in this run: FP64 FMA throughput of fdtd_alu_probe (independent "
+                               "FMA chains on every SM, CUDA events)",
+                "flops_per_update": FLOPS_PER_UPDATE_F64, "updates_per_launch": upd_launch, "launch_ms": avg_ms,
+                "traffic": 32.1 * upd_launch,
+                "traffic_source": "ncu dram__bytes_read+write of k_march_f64 at nx 2^20, D 100 (32.1 B/update), "
+                                  "scaled to this launch's updates",
+                "hbm": hbm}
+    else:
+        # FP32-pipe work of a bulk update of the double-float march, from ncu's executed
+        # FADD/FMUL/FFMA counts of k_march_dw over one launch (see DW_* constants)
+        ach = DW_FP32_INSTR_PER_UPDATE * upd_launch / (avg_ms * 1e-3) / 1e12
+        pk = alu_peaks["fp32"] / 2  # FMA rate = FP32 pipe instruction rate
+        roof = {"kernel": "k_march_dw", "bound": "alu", "achieved": ach, "peak": pk,
+                "unit": "T FP32-pipe instructions/s (FADD, FMUL, FFMA each 1)", "frac": ach / pk,
+                "peak_source": "measured in this run: FP32 FMA throughput of fdtd_alu_probe / 2 flops per FMA",
+                "fp32_instr_per_update": DW_FP32_INSTR_PER_UPDATE, "flops_per_update": DW_FLOPS_PER_UPDATE,
+                "flops_frac": DW_FLOPS_PER_UPDATE * upd_launch / (avg_ms * 1e-3) / alu_peaks["fp32"],
+                "updates_per_launch": upd_launch, "launch_ms": avg_ms, "traffic": None,
+                "traffic_source": "no ncu capture of this kernel at this size yet", "hbm": hbm}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "vs_baseline": None, "dtype": "f64" if prec == fdtd.F64 else "f32x2 (double-float, FP64-accurate)",
+           "data": "synthetic",
            "config": {"workload": w.name, "nx": w.nx, "nt": w.nt, "D": w.D, "delta": w.delta,
-                      "k0a": w.omega0 * w.a, "sigma": w.sigma, "precision": "complex128",
+                      "k0a": w.omega0 * w.a, "sigma": w.sigma,
+                      "precision": "complex128" if prec == fdtd.F64 else "complex double-float (4 x FP32)",
                       "rows_per_launch": rpl, "parallelism": f"replicas x{world}",
                       "l2": "inputs larger than L2 (ring of D+2 rows = "
                             f"{(w.D + 2) * w.nx * 16 / 1e9:.1f} GB)"},
@@ -414,9 +442,11 @@ def run_variant(args):
     ms = start.elapsed_time(stop)
     t_bnd = sum(a.elapsed_time(b) for a, b, _ in ev) / len(ev)
     t_march = sum(b.elapsed_time(c) for _, b, c in ev) / len(ev)
-    # error against the FP64 march (parity-checked against the oracle) on up to 4 instances:
-    # the batch plan's norms, and about 512 stored rows of each instance marched alone
-    pick = sorted(range(len(ws_list)), key=lambda i: ws_list[i].updates)[:4]
+    # error against the FP64 march (parity-checked against the oracle) on the three largest
+    # instances by updates (the longest characteristics) and the smallest: the batch plan's
+    # norms, and about 512 stored rows of each instance marched alone
+    order = sorted(range(len(ws_list)), key=lambda i: ws_list[i].updates)
+    pick = sorted(set(order[-3:] + order[:1]))
     errs, nerrs = [], []
     for i in pick:
         w = ws_list[i]
@@ -468,8 +498,12 @@ def run_variant(args):
                         "bytes_per_update": 16, "launch_ms": t_march, "peak_source": src},
            "boundary_ms": t_bnd, "march_ms": t_march,
            "error_vs_fp64": {"instances": pick, "stored_rows_rel_l2_max": max(errs), "norms_rel_max": max(nerrs),
-                             "how": "~512 stored rows of each instance marched alone in complex64 and FP64; "
-                                    "norms of the timed plan vs FP64"},
+                             "per_instance": [{"i": i, "nx": ws_list[i].nx, "nt": ws_list[i].nt, "D": ws_list[i].D,
+                                               "rel_l2": e, "norms_rel": ne}
+                                              for i, e, ne in zip(pick, errs, nerrs)],
+                             "how": "~512 stored rows of each instance (the 3 largest by updates and the "
+                                    "smallest) marched alone in complex64 and FP64; norms of the timed plan "
+                                    "vs FP64"},
            "clocks": clocks}
     if f64:
         out["fp64_same_instances"] = f64

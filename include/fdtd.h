@@ -18,7 +18,8 @@
  * the paper's n_x).  Marched columns are m = -D/2+1 .. -D/2+nx (index
  * j = m + D/2 - 1 in every buffer below), rows n = 0 .. nt-1.  Row 0 is the
  * initial condition psi(x>-a, 0) = 0.  Complex values are interleaved
- * (re, im): complex128 for FDTD_F64, complex64 for FDTD_F32_COMP.
+ * (re, im): complex128 for FDTD_F64 and FDTD_F64_DW, complex64 for
+ * FDTD_F32_COMP.
  *
  * Memory.  The library never allocates device memory.  fdtd_plan reports the
  * workspace size; the caller allocates it (any allocator) and lends it with
@@ -62,8 +63,12 @@ typedef enum {
 
 typedef enum {
   FDTD_F64 = 0,       /* complex128 march                                          */
-  FDTD_F32_COMP = 1   /* complex64 march with compensated increments; the boundary */
+  FDTD_F32_COMP = 1,  /* complex64 march with compensated increments; the boundary */
                       /* tables and the norm reduction stay FP64                   */
+  FDTD_F64_DW = 2     /* the FP64 march's results (same tolerance against the FP64 */
+                      /* oracle) computed in double-float arithmetic: each value a */
+                      /* pair of FP32 numbers (48 significant bits) on the FP32    */
+                      /* pipes; readouts are complex128, as for FDTD_F64           */
 } fdtd_precision;
 
 typedef enum {
@@ -97,12 +102,22 @@ typedef struct {
                          /* marches a wide instance, 1..8; 0 = by the widest one  */
   int32_t mid_weight;    /* column split: cost of a column of -a < x <= 3a in     */
                          /* bulk columns, 1..4096; 0 = 16                          */
+  int64_t max_probes;    /* FDTD_F64 / FDTD_F64_DW: capacity of fdtd_set_probes;  */
+                         /* 0 = none                                              */
+  int64_t spin_cycles;   /* bound of the march's waits on other CTAs, in SM clock */
+                         /* cycles; 0 = 4e9 (~2 s).  A wait that runs out latches */
+                         /* FDTD_ERR_TIMEOUT and the march stops (the next        */
+                         /* fdtd_readout returns it).  A small value is for tests */
+                         /* of that path.                                          */
 } fdtd_params;
 
 /* fdtd_set_boundary sources */
 enum {
   FDTD_BOUNDARY_ANALYTIC = 0, /* e(t) by the library's gamma(n,z) / quadrature kernel */
-  FDTD_BOUNDARY_TABLE = 1     /* e(r delta), r = 0..nt-1, complex128, given on device */
+  FDTD_BOUNDARY_TABLE = 1,    /* e(r delta), r = 0..nt-1, complex128, given on device */
+  FDTD_BOUNDARY_RESTORE = 2   /* analytic boundary, then resume from a checkpoint     */
+                              /* (FDTD_READ_STATE of a plan with the same parameters;*/
+                              /* any memory, n = its size in bytes)                  */
 };
 
 /* fdtd_readout kinds */
@@ -111,7 +126,22 @@ enum {
   FDTD_READ_NORMS = 1,     /* N(n) for n = 0..rows_done-1: FP64                     */
   FDTD_READ_SNAPSHOTS = 2, /* rows 0, tstep+1, 2(tstep+1), ... marched so far       */
   FDTD_READ_ETABLE = 3,    /* e(r delta), r = 0..nt-1: complex128                   */
-  FDTD_READ_ROWS_DONE = 4  /* int64: rows available (row 0 counts)                  */
+  FDTD_READ_ROWS_DONE = 4, /* int64: rows available (row 0 counts)                  */
+  FDTD_READ_STATE = 6,     /* checkpoint: the rows the march still reads (the last  */
+                           /* min(rows, D+2), in the plan's storage format), the    */
+                           /* compensation remainders (FDTD_F32_COMP), the norms    */
+                           /* so far, behind a header of the parameters; a batched  */
+                           /* plan gives one such record per instance (by           */
+                           /* fdtd_readout_instance).  Snapshots are not included.  */
+  FDTD_READ_PROBES = 7,    /* psi at the points of fdtd_set_probes, complex128, in  */
+                           /* the order given (0 where the march has not yet been)  */
+  FDTD_READ_MEASURES = 5   /* App. D, per snapshot row n marched so far: 4 doubles  */
+                           /* (Re mu, Im mu, lambda, det M = |mu|^2 lambda); needs   */
+                           /* FDTD_IC_STIM_EMISSION, tstep >= 0, FDTD_F64/F64_DW.    */
+                           /* mu(t) = int phi* psi dx with phi the one-excitation    */
+                           /* photon (free packet minus the emission of the atom and */
+                           /* its mirror image), lambda(t) = int |psi|^2 dx - |e0|^2; */
+                           /* x <= -a exact, x > -a by the trapezoid rule            */
 };
 
 /*
@@ -145,8 +175,14 @@ fdtd_status fdtd_bind_workspace(fdtd_plan_t plan, void* device_ptr, size_t bytes
  * wavepacket table phi(-a - j delta), the per-row source scalars, and zeroes
  * the ring.  source = FDTD_BOUNDARY_TABLE takes e(r delta) from device_table
  * (n = nt complex128 values, device memory, read during the call's kernels)
- * instead of computing it.  Asynchronous.  Errors: FDTD_ERR_STATE (no
- * workspace), FDTD_ERR_INVALID_ARG, FDTD_ERR_CUDA.
+ * instead of computing it.  Asynchronous.  source = FDTD_BOUNDARY_RESTORE
+ * builds the analytic boundary and then loads a checkpoint (device_table: the
+ * FDTD_READ_STATE bytes of a plan with the same parameters, host or device
+ * memory, n = their size; for a batched plan the records of every instance in
+ * order); the march resumes at the checkpoint's row, and continuing it gives
+ * bitwise the results of the uninterrupted march.  This source synchronises
+ * the stream.  Errors: FDTD_ERR_STATE (no workspace), FDTD_ERR_INVALID_ARG
+ * (including a checkpoint of other parameters or cut short), FDTD_ERR_CUDA.
  */
 fdtd_status fdtd_set_boundary(fdtd_plan_t plan, int32_t source, const void* device_table, int64_t n);
 
@@ -181,6 +217,20 @@ fdtd_status fdtd_march_graph(fdtd_plan_t plan, int64_t n_rows);
  * boundary value) .. the last marched column, accumulated in FP64 (App. D).
  */
 fdtd_status fdtd_readout(fdtd_plan_t plan, int32_t kind, void* dst, int64_t dst_bytes);
+
+/*
+ * fdtd_set_probes -- points at which the march records psi as it completes
+ * their rows (Table 1's save_chi output and Eq. 2 need psi at chosen retarded
+ * points, not whole rows).  points: host memory, count pairs (n, j) of row
+ * n in [0, nt) and column index j in [0, nx) (x = (j + 1 - D/2) delta), in any
+ * order, repeats allowed; count <= max_probes of the plan.  Call after
+ * fdtd_set_boundary (which clears the probes); points on rows marched before
+ * the call read 0.  FDTD_READ_PROBES returns the values in the order given.
+ * FDTD_F64 and FDTD_F64_DW plans.  Errors: FDTD_ERR_STATE (no boundary),
+ * FDTD_ERR_INVALID_ARG (a point outside the box, count > max_probes),
+ * FDTD_ERR_UNSUPPORTED (FDTD_F32_COMP plans), FDTD_ERR_CUDA.
+ */
+fdtd_status fdtd_set_probes(fdtd_plan_t plan, const int64_t* points, int64_t count);
 
 /* Size in bytes that fdtd_readout(kind) writes at the current state. */
 int64_t fdtd_readout_bytes(fdtd_plan_t plan, int32_t kind);
@@ -222,29 +272,30 @@ fdtd_status fdtd_gamma_star(const int32_t* n, const double* z, double* out, int6
  * has no counterpart; this is a deployment convenience.
  *
  * Who cannot allocate: a host framework that owns all device memory through
- * its own pool and forbids other allocations, a plugin inside such a process,
- * or code that runs while a stream is being captured into a CUDA graph
- * (allocation calls are not allowed during capture).  They can pass inputs
- * and outputs, but cannot lend the march its scratch (fdtd_bind_workspace).
+ * its own pool and forbids other allocations, or a plugin inside such a
+ * process that may use only the buffers the host hands it.  They can pass
+ * inputs and outputs, but cannot lend the march its scratch
+ * (fdtd_bind_workspace).
  *
  * Scratch: a 64 MiB array built into the library (fdtd_noalloc_max_bytes()),
  * placed on every GPU that loads the library and held there until the process
- * exits.  An instance whose workspace (as fdtd_plan reports it) exceeds that
- * size is rejected with FDTD_ERR_WORKSPACE before any device work.  Every call
- * on a device shares the array: calls whose work overlaps on the GPU (other
- * streams, other host threads) race and corrupt each other; serialise them.
- * Each call zeroes the ring, norms and barrier words it uses, so a call does
- * not see the previous call's contents.
+ * exits.  An instance whose workspace (as fdtd_plan reports it, without
+ * snapshots) exceeds that size is rejected with FDTD_ERR_WORKSPACE before any
+ * device work.  Every call on a device shares the array: calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and corrupt
+ * each other; serialise them.  Each call zeroes the ring, norms and barrier
+ * words it uses, so a call does not see the previous call's contents.
  *
  * Set-up: the first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current).  Make that first call
- * before any stream capture.  No call allocates device memory, and none calls
- * cudaMalloc, cudaFree or an allocating library routine.
+ * (cudaGetSymbolAddress, with that device current).  No call allocates device
+ * memory, and none calls cudaMalloc, cudaFree or an allocating library
+ * routine.  The call is blocking: it synchronises cuda_stream before it
+ * returns, on success and on every error after work was queued, so no work
+ * of a failed call is left running on the shared array.
  *
  *   p          : parameters, as for fdtd_plan (precision FDTD_F64; tstep is
  *                ignored: no snapshots are kept).
- *   cuda_stream: cudaStream_t for all work; the call synchronises it before
- *                returning, to report device-side errors.
+ *   cuda_stream: cudaStream_t for all work.
  *   row_out    : device memory, nx complex128: psi on the last row nt-1.
  *   norms_out  : device memory, nt doubles: N(n) as FDTD_READ_NORMS defines it.
  * Errors: as fdtd_plan / fdtd_set_boundary / fdtd_march / fdtd_readout, plus
@@ -254,6 +305,28 @@ fdtd_status fdtd_march_noalloc(const fdtd_params* p, void* cuda_stream, void* ro
 
 /* Size in bytes of the built-in scratch of fdtd_march_noalloc. */
 size_t fdtd_noalloc_max_bytes(void);
+
+/*
+ * fdtd_geometric_measure -- the geometric non-Markovianity measure of App. D,
+ *   N_geo = integral of d|det M_t|/dt over the times where it is positive,
+ * from samples det_m[0..n) of det M_t (FDTD_READ_MEASURES, 4th column), as the
+ * sum of the increases of |det M| between consecutive samples.  Host memory,
+ * host code.  Errors: FDTD_ERR_INVALID_ARG (NULL, n < 0).
+ */
+fdtd_status fdtd_geometric_measure(const double* det_m, int64_t n, double* out);
+
+/*
+ * fdtd_alu_probe -- measured arithmetic peak of the current GPU, the
+ * denominator of the marches' arithmetic roofline (the paper has no
+ * counterpart; its march is memory-bound on CPUs).
+ *   kind       : 0 FP64 FMA, 1 FP32 FMA, 2 packed FP32 pairs (fma.rn.f32x2).
+ *   cuda_stream: stream the probe kernels run on (one untimed, one timed
+ *                launch of independent FMA chains on every SM).
+ *   flops_per_s (out): 2 flops per FMA (4 per packed FMA) over the timed
+ *                launch, measured with CUDA events; the call synchronises.
+ * Errors: FDTD_ERR_INVALID_ARG (kind, NULL), FDTD_ERR_CUDA.
+ */
+fdtd_status fdtd_alu_probe(int32_t kind, void* cuda_stream, double* flops_per_s);
 
 /* ---- surrogate network -----------------------------------------------------
  * The paper has no counterpart: a multilayer perceptron maps a few physical

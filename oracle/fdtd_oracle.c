@@ -27,6 +27,8 @@
  *                    as the boundary (Sec. 2, "boundary needs only x<-a").
  *   orc_march_left   the same update marched inside x <= -a (validation test 1
  *                    of Sec. 4), with an exact band to its left.
+ *   orc_chi          the two-photon wavefunction chi(x1, x2, t) of Eq. 2 from
+ *                    the marched psi (the save_chi output of Table 1).
  *   orc_measures     mu(t), lambda(t) and det M_t of the non-Markovian measure
  *                    (App. D) from the march's snapshot rows and norms, with the
  *                    one-excitation photon phi(x,t) (orc_phi1) and atom e0(t).
@@ -720,6 +722,64 @@ int orc_measures(const orc_params* p, int64_t n_rows, int64_t tstep, const doubl
     out[4 * s + 2] = lam;
     out[4 * s + 3] = creal(mu * conj(mu)) * lam;
   }
+  return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The two-photon wavefunction, Eq. 2.                                        */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * chi(x1, x2, t) by the formal solution Eq. 2 from the marched psi:
+ *   chi = chi(x1-t, x2-t, 0) - (sqrt(Gamma)/2) [ T(x1, x2) + T(x2, x1) ],
+ *   T(y1, y2) = psi(y1-y2-a, t-y2-a) theta(y2+a) theta(t-y2-a)
+ *             - psi(y1-y2+a, t-y2+a) theta(y2-a) theta(t-y2+a),
+ * theta(0) = 1/2, on grid points x1 = i1 delta, x2 = i2 delta, t = n delta
+ * (pts: count triples (i1, i2, n)).  psi(x <= -a) is the exact C phi(x-t) e(t);
+ * psi(x > -a) is read from grid (rows 0 .. n_rows-1 of the march, nx columns
+ * each, interleaved complex).  A psi argument to the right of the box or above
+ * the last row gives ORC_BAD_READ.  out: count complex values.
+ */
+int orc_chi(const orc_params* p, int64_t n_rows, const double* grid, const int64_t* pts, int64_t count,
+            double* out) {
+  int st = check_params(p);
+  if (st != ORC_OK) return st;
+  if (n_rows < 1 || n_rows > p->nt) return ORC_BAD_ARG;
+  const int64_t Dh = p->D / 2;
+  const double dl = p->delta, C = psi_prefactor(p);
+  const cplx* g = (const cplx*)grid;
+  cplx* et = (cplx*)malloc(sizeof(cplx) * (size_t)n_rows);
+  if (!et) return ORC_NO_MEM;
+  st = orc_etable(p, n_rows, (double*)et);
+  int bad = 0;
+  /* psi at column c (x = c delta), row r */
+  #define ORC_PSI(c, r, dst)                                                        \
+    do {                                                                            \
+      if ((r) < 0) { dst = 0; break; }                                              \
+      if ((r) >= n_rows) { bad = 1; dst = 0; break; }                               \
+      if ((c) <= -Dh) dst = C * phi_at(p, (double)((c) - (r)) * dl) * et[r];        \
+      else if ((c) - (-Dh + 1) >= p->nx) { bad = 1; dst = 0; }                     \
+      else dst = g[(r) * p->nx + ((c) - (-Dh + 1))];                                \
+    } while (0)
+  for (int64_t q = 0; q < count; ++q) {
+    const int64_t i1 = pts[3 * q], i2 = pts[3 * q + 1], n = pts[3 * q + 2];
+    cplx T[2] = {0, 0};
+    for (int sw = 0; sw < 2; ++sw) {
+      const int64_t y1 = sw ? i2 : i1, y2 = sw ? i1 : i2;
+      const int64_t ra = n - y2 - Dh, rb = n - y2 + Dh; /* t - y2 - a, t - y2 + a */
+      const double wa = theta_half(y2 + Dh) * theta_half(ra), wb = theta_half(y2 - Dh) * theta_half(rb);
+      cplx va = 0, vb = 0;
+      if (wa > 0.0) ORC_PSI(y1 - y2 - Dh, ra, va);
+      if (wb > 0.0) ORC_PSI(y1 - y2 + Dh, rb, vb);
+      T[sw] = wa * va - wb * vb;
+    }
+    const cplx v = chi0(p, (double)(i1 - n) * dl, (double)(i2 - n) * dl) - 0.5 * sqrt(p->gamma) * (T[0] + T[1]);
+    out[2 * q] = creal(v);
+    out[2 * q + 1] = cimag(v);
+  }
+  #undef ORC_PSI
+  free(et);
+  if (bad) return ORC_BAD_READ;
   return st;
 }
 

@@ -74,8 +74,9 @@ def lib():
         L.orc_e0_at.argtypes = [P, ctypes.c_double, dp, dp]
         L.orc_measures.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p]
+        L.orc_chi.argtypes = [P, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
         for f in (L.orc_G, L.orc_P, L.orc_phi, L.orc_e_at, L.orc_etable, L.orc_march, L.orc_march_left,
-                  L.orc_psi_exact, L.orc_phi1, L.orc_e0_at, L.orc_measures):
+                  L.orc_psi_exact, L.orc_phi1, L.orc_e0_at, L.orc_measures, L.orc_chi):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -218,4 +219,16 @@ def measures(p: Params, march_out: dict, tstep: int) -> np.ndarray:
     cp = p.c()
     _check(lib().orc_measures(ctypes.byref(cp), n_rows, tstep, snaps.ctypes.data, norms.ctypes.data,
                               out.ctypes.data), "orc_measures")
+    return out
+
+
+def chi(p: Params, grid: np.ndarray, pts) -> np.ndarray:
+    """chi(i1 delta, i2 delta, n delta) by Eq. 2 for triples (i1, i2, n), from the
+    march's full grid (tstep = 0 snapshots, rows 0 .. n_rows-1)."""
+    g = np.ascontiguousarray(grid, dtype=np.complex128)
+    q = np.ascontiguousarray(pts, dtype=np.int64).reshape(-1, 3)
+    out = np.zeros(q.shape[0], dtype=np.complex128)
+    cp = p.c()
+    _check(lib().orc_chi(ctypes.byref(cp), g.shape[0], g.ctypes.data, q.ctypes.data, q.shape[0], out.ctypes.data),
+           "orc_chi")
     return out

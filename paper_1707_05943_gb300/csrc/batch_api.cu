@@ -72,7 +72,7 @@ fdtd_status validate(const fdtd_params& p) {
   if (p.init_cond < FDTD_IC_STIM_EMISSION || p.init_cond > FDTD_IC_TWO_PHOTON_GAUSS) return FDTD_ERR_INVALID_ARG;
   if (p.init_cond != FDTD_IC_TWO_PHOTON_GAUSS && !(p.alpha > 0)) return FDTD_ERR_INVALID_ARG;
   if (p.init_cond == FDTD_IC_TWO_PHOTON_GAUSS && !(p.sigma > 0)) return FDTD_ERR_INVALID_ARG;
-  if (p.tstep < -1 || p.rows_per_launch < 0) return FDTD_ERR_INVALID_ARG;
+  if (p.tstep < -1 || p.rows_per_launch < 0 || p.spin_cycles < 0) return FDTD_ERR_INVALID_ARG;
   if (p.cluster_ctas < 0 || p.cluster_ctas > 8 || p.mid_weight < 0 || p.mid_weight > 4096) return FDTD_ERR_INVALID_ARG;
   if (p.precision != FDTD_F32_COMP) return FDTD_ERR_INVALID_ARG;
   return FDTD_OK;
@@ -180,8 +180,10 @@ fdtd_status batch_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n, v
 
 fdtd_status batch_set_boundary(fdtd_plan_s* P, int32_t source, const void* table, int64_t ntab) {
   const int n = (int)P->inst.size();
-  if (source != FDTD_BOUNDARY_ANALYTIC && source != FDTD_BOUNDARY_TABLE)
+  if (source != FDTD_BOUNDARY_ANALYTIC && source != FDTD_BOUNDARY_TABLE && source != FDTD_BOUNDARY_RESTORE)
     return fail(P, FDTD_ERR_INVALID_ARG, "unknown boundary source");
+  if (source == FDTD_BOUNDARY_RESTORE && (!table || ntab <= 0))
+    return fail(P, FDTD_ERR_INVALID_ARG, "checkpoint missing");
   int64_t total_nt = 0;
   for (auto& b : P->inst) total_nt += b.p.nt;
   if (source == FDTD_BOUNDARY_TABLE && (!table || ntab != total_nt))
@@ -236,7 +238,7 @@ fdtd_status batch_set_boundary(fdtd_plan_s* P, int32_t source, const void* table
     max_nt = std::max<int64_t>(max_nt, p.nt);
   }
   // e(t) of every instance in one launch per pass (FP64)
-  if (source == FDTD_BOUNDARY_ANALYTIC) {
+  if (source != FDTD_BOUNDARY_TABLE) {
     e = cudaMemcpyAsync(P->ws + P->off_eargs, eargs.data(), sizeof(fdtd::EtabArgs) * (size_t)n,
                         cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = fdtd::launch_etable_batch(at<fdtd::EtabArgs>(P, P->off_eargs), n, max_nt, s);
@@ -264,13 +266,21 @@ fdtd_status batch_set_boundary(fdtd_plan_s* P, int32_t source, const void* table
     d.mid_weight = P->mid_weight;
     d.tstep = p.tstep;
     auto f = [](cd v) { return make_float2((float)v.re, (float)v.im); };
-    d.d1 = f(cd{b.c1.re - 1.0, b.c1.im});
+    auto flo = [](cd v) {  // the part of v that its FP32 rounding drops
+      return make_float2((float)(v.re - (double)(float)v.re), (float)(v.im - (double)(float)v.im));
+    };
+    const cd d1 = cd{b.c1.re - 1.0, b.c1.im};
+    d.d1 = f(d1);
     d.c2 = f(b.c2);
     d.c3 = f(b.c3);
+    d.d1lo = flo(d1);
+    d.c2lo = flo(b.c2);
+    d.c3lo = flo(b.c3);
     d.gs = f(b.gs);
     cd pw = cd{1.0, 0.0};
     for (int k = 0; k <= fdtd::kF32MaxTrunc; ++k) {
       d.c2pow[k] = f(pw);
+      d.c2powlo[k] = flo(pw);
       pw = pw * b.c2;
     }
     d.C = b.C;
@@ -317,13 +327,23 @@ fdtd_status batch_set_boundary(fdtd_plan_s* P, int32_t source, const void* table
   }
   P->nitems = (int)items.size();
   if (P->nclusters > P->nitems) P->nclusters = P->nitems;
+  if (source == FDTD_BOUNDARY_RESTORE) {
+    // each instance resumes at its checkpoint's row (rings, remainders, norms loaded)
+    std::vector<int64_t> done(n, 1);
+    fdtd_status st = state_restore(P, table, ntab, s, done.data());
+    if (st != FDTD_OK) {
+      P->state = 1;
+      return fail(P, st, "checkpoint does not match the plan's parameters, is cut short, or cannot be read");
+    }
+    for (int i = 0; i < n; ++i) desc[i].range[0] = desc[i].range[1] = done[i];
+  }
   e = cudaMemcpyAsync(P->ws + P->off_desc, desc.data(), sizeof(fdtd::InstDesc) * (size_t)n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(P->ws + P->off_order, items.data(), sizeof(fdtd::WorkItem) * items.size(),
                         cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(P, e, "cudaMemcpyAsync(descriptors)");
   // the pageable copies above are staged before they return
-  P->rows_done = 1;
+  P->rows_done = P->inst[0].rows_done;
   P->state = 2;
   return FDTD_OK;
 }
@@ -421,6 +441,7 @@ int64_t batch_readout_bytes(fdtd_plan_s* P, int32_t i, int32_t kind) {
     }
     case FDTD_READ_ETABLE: return (int64_t)sizeof(cd) * b.p.nt;
     case FDTD_READ_ROWS_DONE: return (int64_t)sizeof(int64_t);
+    case FDTD_READ_STATE: return state_bytes(P, i);
   }
   return -1;
 }
@@ -445,6 +466,10 @@ fdtd_status batch_readout(fdtd_plan_s* P, int32_t i, int32_t kind, void* dst, in
     case FDTD_READ_SNAPSHOTS: src = P->ws + b.off_snaps; break;
     case FDTD_READ_ETABLE: src = P->ws + b.off_etab; break;
     case FDTD_READ_ROWS_DONE: memcpy(dst, &b.rows_done, sizeof(int64_t)); return FDTD_OK;
+    case FDTD_READ_STATE: {
+      fdtd_status st = state_readout(P, i, dst, dst_bytes, P->stream);
+      return st == FDTD_OK ? FDTD_OK : fail(P, st, "checkpoint copy");
+    }
   }
   if (need > 0) {
     e = cudaMemcpyAsync(dst, src, (size_t)need, cudaMemcpyDefault, P->stream);

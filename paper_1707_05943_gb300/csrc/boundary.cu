@@ -372,6 +372,19 @@ cudaError_t launch_boundary(const BoundaryArgs& a, cd* hscratch, bool compute_et
   return launch_boundary_post(a, s);
 }
 
+// e0 of the one-excitation sector for the exponential packet of a stimulated-
+// emission plan (the atom starting in its ground state; App. D uses it): the
+// two-photon-class e-table passes with the same photon, written to e0tab
+cudaError_t launch_etable_e0(const BoundaryArgs& a, cd* e0tab, cd* hscratch, cudaStream_t s) {
+  BoundaryArgs b = a;
+  b.init_cond = FDTD_IC_TWO_PHOTON_EXP;
+  b.etab = e0tab;
+  EtabArgs E = etable_args(b, hscratch);
+  k_etable_pass1<<<(unsigned)((a.nt + 63) / 64), 64, 0, s>>>(E);
+  k_etable_pass2<<<(unsigned)((a.nt + 127) / 128), 128, 0, s>>>(E);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gamma_star(const int32_t* n, const double* z, double* out, int64_t count, cudaStream_t s) {
   if (count == 0) return cudaSuccess;
   const int T = 128;

@@ -5,8 +5,10 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#include <stdint.h>
 
 #include <new>
+#include <vector>
 
 #include "fdtd_internal.cuh"
 
@@ -37,11 +39,11 @@ cd cdiv(cd a, cd b) {
 }
 double cabsh(cd a) { return hypot(a.re, a.im); }
 
-// smallest k >= 1 with |x|^k < 2^-60 (x != 0), capped
-int trunc_depth(double ax, int cap) {
+// smallest k >= 1 with |x|^k < 2^-bits (x != 0), capped
+int trunc_depth(double ax, int cap, int bits) {
   if (ax <= 0.0) return 1;
   if (ax >= 1.0) return cap + 1;
-  double k = ceil(-60.0 * log(2.0) / log(ax));
+  double k = ceil(-(double)bits * log(2.0) / log(ax));
   if (k < 1) k = 1;
   return (k > cap) ? cap + 1 : (int)k;
 }
@@ -49,6 +51,85 @@ int trunc_depth(double ax, int cap) {
 template <class T>
 T* at(fdtd_plan_t p, size_t off) {
   return reinterpret_cast<T*>(p->ws + off);
+}
+
+// Dependency lists of the double-float march (march_dw.cu).  For each CTA b,
+// every other CTA whose columns b reads, with the smallest lag at which it
+// reads them (row n of b reads row n - lag of that CTA); and, transposed, the
+// CTAs that read b.  The reads of a column j (buffer index) of row n:
+//   j-1, j at lag 1 (stencil; the carry halo of khalo columns left of the
+//   CTA's first column recomputes those columns too);
+//   j-D-1, j-D at lag D (delay square, rows n-D and n-D-1);
+//   for j < D: D-2-j, D-1-j at lag j+1 (mirror bar of line 2, row n-m-D/2);
+//   for D <= j < 2D: 2D-2-j, 2D-1-j at lag j-D+1 (mirror bar of line 3,
+//   row n-m+D/2).
+// Columns outside [0, nx) are x <= -a (exact) and need nothing.
+struct DwDeps {
+  std::vector<int> dep_off, rd_off, rd;
+  std::vector<int2> dep;
+};
+DwDeps build_dw_deps(const int64_t* split, int G, int64_t nx, int D, int khalo) {
+  auto owner = [&](int64_t col) {
+    int lo = 0, hi = G;  // last b with split[b] <= col
+    while (hi - lo > 1) {
+      int mid = (lo + hi) / 2;
+      if (split[mid] <= col) lo = mid; else hi = mid;
+    }
+    return lo;
+  };
+  std::vector<std::vector<int>> lag(G, std::vector<int>());
+  DwDeps d;
+  d.dep_off.assign(G + 1, 0);
+  std::vector<std::vector<int>> readers(G);
+  for (int b = 0; b < G; ++b) {
+    const int64_t jl = split[b], jh = split[b + 1];
+    std::vector<int> best(G, INT32_MAX);
+    if (jl < jh) {
+      const int64_t h0 = jl - khalo > 0 ? jl - khalo : 0;
+      auto mark_range = [&](int64_t c0, int64_t c1, int L) {  // columns [c0, c1)
+        if (c0 < 0) c0 = 0;
+        if (c1 > nx) c1 = nx;
+        if (c0 >= c1) return;
+        for (int o = owner(c0); o < G && split[o] < c1; ++o)
+          if (split[o] < split[o + 1] && L < best[o]) best[o] = L;
+      };
+      mark_range(h0 - 1, jh, 1);
+      mark_range(h0 - D - 1, jh - D, D);
+      for (int64_t j = h0; j < jh && j < 2 * (int64_t)D; ++j) {
+        if (j < D) mark_range(D - 2 - j, D - j, (int)(j + 1));
+        else mark_range(2 * (int64_t)D - 2 - j, 2 * (int64_t)D - j, (int)(j - D + 1));
+      }
+    }
+    for (int o = 0; o < G; ++o)
+      if (o != b && best[o] != INT32_MAX) {
+        d.dep.push_back(make_int2(o, best[o]));
+        readers[o].push_back(b);
+      }
+    d.dep_off[b + 1] = (int)d.dep.size();
+  }
+  d.rd_off.assign(G + 1, 0);
+  for (int b = 0; b < G; ++b) {
+    for (int r : readers[b]) d.rd.push_back(r);
+    d.rd_off[b + 1] = (int)d.rd.size();
+  }
+  return d;
+}
+
+// the probe arrays in the workspace: row offsets, columns, output positions, values
+struct ProbeView {
+  int* off;
+  int* col;
+  int* idx;
+  double2* val;
+};
+ProbeView probe_view(fdtd_plan_t P) {
+  ProbeView v;
+  v.off = reinterpret_cast<int*>(P->ws + P->off_probes);
+  v.col = v.off + P->p.nt + 1;
+  v.idx = v.col + P->p.max_probes;
+  const size_t vb = align_up(sizeof(int) * (size_t)(P->p.nt + 1 + 2 * P->p.max_probes) + 16);
+  v.val = reinterpret_cast<double2*>(P->ws + P->off_probes + vb);
+  return v;
 }
 
 }  // namespace
@@ -86,16 +167,18 @@ fdtd_status fdtd_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n_ins
   if (p.init_cond < FDTD_IC_STIM_EMISSION || p.init_cond > FDTD_IC_TWO_PHOTON_GAUSS) return FDTD_ERR_INVALID_ARG;
   if (p.init_cond != FDTD_IC_TWO_PHOTON_GAUSS && !(p.alpha > 0)) return FDTD_ERR_INVALID_ARG;
   if (p.init_cond == FDTD_IC_TWO_PHOTON_GAUSS && !(p.sigma > 0)) return FDTD_ERR_INVALID_ARG;
-  if (p.tstep < -1 || p.rows_per_launch < 0) return FDTD_ERR_INVALID_ARG;
+  if (p.tstep < -1 || p.rows_per_launch < 0 || p.spin_cycles < 0) return FDTD_ERR_INVALID_ARG;
   if (p.cluster_ctas < 0 || p.cluster_ctas > 8 || p.mid_weight < 0 || p.mid_weight > 4096) return FDTD_ERR_INVALID_ARG;
-  if (p.precision != FDTD_F64) return FDTD_ERR_UNSUPPORTED;
+  if (p.max_probes < 0 || p.max_probes > INT32_MAX || p.nt >= INT32_MAX) return FDTD_ERR_INVALID_ARG;
+  if (p.precision != FDTD_F64 && p.precision != FDTD_F64_DW) return FDTD_ERR_UNSUPPORTED;
 
   P->p = p;
+  P->dw = (p.precision == FDTD_F64_DW);
   P->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   cudaError_t e = cudaGetDevice(&P->device);
   if (e != cudaSuccess) return FDTD_ERR_CUDA;
   cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
-  int maxg = fdtd::march_f64_max_grid(P->device);
+  int maxg = P->dw ? fdtd::march_dw_max_grid(P->device) : fdtd::march_f64_max_grid(P->device);
   if (maxg <= 0) return FDTD_ERR_CUDA;
   // one CTA per SM, but at least 64 columns per CTA
   int grid = P->num_sms < maxg ? P->num_sms : maxg;
@@ -116,13 +199,16 @@ fdtd_status fdtd_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n_ins
   P->C = (p.init_cond == FDTD_IC_STIM_EMISSION) ? 1.0 : sqrt(2.0);
 
   const double ac2 = cabsh(P->c2);
-  P->kfix = trunc_depth(ac2, fdtd::kMaxTrunc);
+  // carries are exact while |c2|^k stays above the arithmetic's rounding:
+  // 2^-60 in FP64, 2^-52 in double-float (48 significant bits)
+  P->kfix = trunc_depth(ac2, fdtd::kMaxTrunc, P->dw ? 52 : 60);
   P->khalo = P->kfix;
   if (P->kfix > fdtd::kMaxTrunc)
     return FDTD_ERR_UNSUPPORTED;  // |c2| too close to 1 (delta far too coarse)
 
   // workspace layout
-  P->R = p.D + 2;
+  P->R = p.D + 2 + (P->dw ? fdtd::kDwSlack : 0);
+  P->rows_per_launch = p.rows_per_launch > 0 ? p.rows_per_launch : 4096;
   P->elem = sizeof(cd);
   // row pitch: a multiple of 32 columns plus 32, so that ring rows are never a
   // power-of-two number of bytes apart (rows read together would share L2 slices)
@@ -137,8 +223,25 @@ fdtd_status fdtd_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n_ins
   P->off_detab = off;    off = align_up(off + sizeof(cd) * (size_t)(p.nt + p.D));
   P->off_norms = off;    off = align_up(off + sizeof(double) * (size_t)p.nt);
   P->off_hscr = off;     off = align_up(off + sizeof(cd) * (size_t)p.nt);
-  P->off_partials = off; off = align_up(off + 2 * sizeof(double) * (size_t)grid);
+  const size_t npart = P->dw ? (size_t)P->rows_per_launch * (size_t)grid : 2 * (size_t)grid;
+  P->off_partials = off; off = align_up(off + sizeof(double) * npart);
   P->off_colsplit = off; off = align_up(off + sizeof(int64_t) * (size_t)(grid + 1));
+  if (P->dw) {
+    // double-float tables: C e (nt), phi (nphi), R1/R2 (2 nt), dE (nt + D)
+    P->off_dwtab = off;  off = align_up(off + sizeof(float4) * (size_t)(4 * p.nt + P->nphi + p.D));
+    P->off_done = off;   off = align_up(off + sizeof(unsigned long long) * (size_t)grid);
+    P->off_deps = off;   off = align_up(off + sizeof(int) * (size_t)(2 * (grid + 1) + 3 * fdtd::kDwMaxDeps));
+    P->off_rowout = off; off = align_up(off + sizeof(cd) * (size_t)p.nx);
+  }
+  if (p.max_probes > 0) {  // row offsets (nt + 1), columns, output positions, values
+    P->off_probes = off;
+    off = align_up(off + sizeof(int) * (size_t)(p.nt + 1 + 2 * p.max_probes) + 16);
+    off = align_up(off + sizeof(cd) * (size_t)p.max_probes);
+  }
+  if (p.init_cond == FDTD_IC_STIM_EMISSION) {
+    P->off_e0tab = off;  off = align_up(off + sizeof(cd) * (size_t)p.nt);
+    P->off_meas = off;   off = align_up(off + 4 * sizeof(double) * (size_t)P->nsnap);
+  }
   P->off_ring = off;     off = align_up(off + P->elem * (size_t)P->R * (size_t)P->stride);
   P->off_snaps = off;    off = align_up(off + P->elem * (size_t)P->nsnap * (size_t)p.nx);
   P->ws_need = off;
@@ -181,10 +284,12 @@ fdtd_status fdtd_set_boundary(fdtd_plan_t P, int32_t source, const void* device_
   if (P->state < 1) return fail(P, FDTD_ERR_STATE, "fdtd_set_boundary before fdtd_bind_workspace");
   if (P->batched) return batch_set_boundary(P, source, device_table, n);
   const fdtd_params& p = P->p;
-  if (source != FDTD_BOUNDARY_ANALYTIC && source != FDTD_BOUNDARY_TABLE)
+  if (source != FDTD_BOUNDARY_ANALYTIC && source != FDTD_BOUNDARY_TABLE && source != FDTD_BOUNDARY_RESTORE)
     return fail(P, FDTD_ERR_INVALID_ARG, "unknown boundary source");
   if (source == FDTD_BOUNDARY_TABLE && (!device_table || n != p.nt))
     return fail(P, FDTD_ERR_INVALID_ARG, "boundary table must hold nt complex128 values");
+  if (source == FDTD_BOUNDARY_RESTORE && (!device_table || n <= 0))
+    return fail(P, FDTD_ERR_INVALID_ARG, "checkpoint missing");
   cudaStream_t s = P->stream;
   cudaError_t e;
   // zero sync words, ring, norms, snapshots
@@ -200,8 +305,9 @@ fdtd_status fdtd_set_boundary(fdtd_plan_t P, int32_t source, const void* device_
   }
   // column split: equal cost per CTA, with the region -a < x <= 3a (2D columns,
   // read through the general path) weighted kMidWeight
-  // (measured: a column of -a < x <= 3a costs ~16 bulk columns in FP64)
-  const int kMidWeight = p.mid_weight > 0 ? p.mid_weight : 16;
+  // (measured: a column of -a < x <= 3a costs ~16 bulk columns in FP64 and
+  // ~20 in double-float, where the pipeline runs at the pace of its slowest CTA)
+  const int kMidWeight = p.mid_weight > 0 ? p.mid_weight : (P->dw ? 20 : 16);
   P->mid_weight = kMidWeight;
   int64_t split[fdtd::kMaxGrid + 1];
   {
@@ -248,10 +354,76 @@ fdtd_status fdtd_set_boundary(fdtd_plan_t P, int32_t source, const void* device_
   a.cs = P->cs;
   a.status = &at<fdtd::SyncWords>(P, P->off_sync)->status;
   a.norms = at<double>(P, P->off_norms);
-  e = fdtd::launch_boundary(a, at<cd>(P, P->off_hscr), source == FDTD_BOUNDARY_ANALYTIC, s);
+  e = fdtd::launch_boundary(a, at<cd>(P, P->off_hscr), source != FDTD_BOUNDARY_TABLE, s);
+  if (e == cudaSuccess && p.init_cond == FDTD_IC_STIM_EMISSION)  // e0 of the measures (App. D)
+    e = fdtd::launch_etable_e0(a, at<cd>(P, P->off_e0tab), at<cd>(P, P->off_hscr), s);
   if (e != cudaSuccess) return cuda_fail(P, e, "boundary kernels");
+  if (P->dw) {
+    float4* t = at<float4>(P, P->off_dwtab);
+    e = fdtd::launch_tables_dw(a.etab, a.phitab, a.rowscal, a.detab, P->C, p.nt, P->nphi, p.D, t, t + p.nt,
+                               t + p.nt + P->nphi, t + 3 * p.nt + P->nphi, s);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(P->ws + P->off_done, 0, sizeof(unsigned long long) * (size_t)P->grid, s);
+    if (e != cudaSuccess) return cuda_fail(P, e, "double-float tables");
+    DwDeps dd = build_dw_deps(split, P->grid, p.nx, p.D, P->khalo);
+    if ((int)dd.dep.size() > fdtd::kDwMaxDeps || (int)dd.rd.size() > fdtd::kDwMaxDeps)
+      return fail(P, FDTD_ERR_UNSUPPORTED, "too many CTA dependencies for the double-float march");
+    // layout: dep_off[G+1] | rd_off[G+1] | dep (int2) | rd (int)
+    std::vector<int> buf(2 * (P->grid + 1) + 3 * fdtd::kDwMaxDeps, 0);
+    memcpy(buf.data(), dd.dep_off.data(), sizeof(int) * (P->grid + 1));
+    memcpy(buf.data() + P->grid + 1, dd.rd_off.data(), sizeof(int) * (P->grid + 1));
+    if (!dd.dep.empty()) memcpy(buf.data() + 2 * (P->grid + 1), dd.dep.data(), sizeof(int2) * dd.dep.size());
+    if (!dd.rd.empty())
+      memcpy(buf.data() + 2 * (P->grid + 1) + 2 * fdtd::kDwMaxDeps, dd.rd.data(), sizeof(int) * dd.rd.size());
+    e = cudaMemcpyAsync(P->ws + P->off_deps, buf.data(), sizeof(int) * buf.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(P, e, "cudaMemcpyAsync(deps)");
+  }
   P->rows_done = 1;
+  P->n_probes = 0;
+  if (source == FDTD_BOUNDARY_RESTORE) {
+    int64_t done = 1;
+    fdtd_status st = state_restore(P, device_table, n, s, &done);
+    if (st != FDTD_OK) {
+      P->state = 1;
+      return fail(P, st, "checkpoint does not match the plan's parameters, is cut short, or cannot be read");
+    }
+    P->rows_done = done;
+  }
   P->state = 2;
+  return FDTD_OK;
+}
+
+fdtd_status fdtd_set_probes(fdtd_plan_t P, const int64_t* points, int64_t count) {
+  if (!P) return FDTD_ERR_INVALID_ARG;
+  if (P->batched) return fail(P, FDTD_ERR_UNSUPPORTED, "probes need an FDTD_F64 or FDTD_F64_DW plan");
+  if (P->state < 2) return fail(P, FDTD_ERR_STATE, "fdtd_set_probes before fdtd_set_boundary");
+  const fdtd_params& p = P->p;
+  if (count < 0 || count > p.max_probes || (count > 0 && !points))
+    return fail(P, FDTD_ERR_INVALID_ARG, "probe count negative or above max_probes");
+  for (int64_t k = 0; k < count; ++k)
+    if (points[2 * k] < 0 || points[2 * k] >= p.nt || points[2 * k + 1] < 0 || points[2 * k + 1] >= p.nx)
+      return fail(P, FDTD_ERR_INVALID_ARG, "probe point outside the marched box");
+  // by row: counting sort of the points, stable in the order given
+  std::vector<int> off(p.nt + 1, 0), col(count > 0 ? count : 1), idx(count > 0 ? count : 1);
+  for (int64_t k = 0; k < count; ++k) ++off[points[2 * k] + 1];
+  for (int64_t n = 0; n < p.nt; ++n) off[n + 1] += off[n];
+  std::vector<int> fill(off.begin(), off.end() - 1);
+  for (int64_t k = 0; k < count; ++k) {
+    const int q = fill[points[2 * k]]++;
+    col[q] = (int)points[2 * k + 1];
+    idx[q] = (int)k;
+  }
+  ProbeView v = probe_view(P);
+  cudaStream_t s = P->stream;
+  cudaError_t e = cudaMemcpyAsync(v.off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && count > 0)
+    e = cudaMemcpyAsync(v.col, col.data(), sizeof(int) * (size_t)count, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && count > 0)
+    e = cudaMemcpyAsync(v.idx, idx.data(), sizeof(int) * (size_t)count, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && count > 0) e = cudaMemsetAsync(v.val, 0, sizeof(double2) * (size_t)count, s);
+  if (e != cudaSuccess) return cuda_fail(P, e, "probe upload");
+  // the pageable copies are staged before cudaMemcpyAsync returns
+  P->n_probes = count;
   return FDTD_OK;
 }
 
@@ -263,6 +435,74 @@ fdtd_status fdtd_march_graph(fdtd_plan_t P, int64_t n_rows) {
   return batch_march_graph(P, n_rows);
 }
 
+// the double-float march of rows [rows_done, end): one persistent launch per
+// rows_per_launch rows, each followed by the FP64 norm reduction of its rows
+static fdtd_status march_dw(fdtd_plan_t P, int64_t end) {
+  const fdtd_params& p = P->p;
+  fdtd::DwArgs a;
+  memset(&a, 0, sizeof a);
+  float4* t = at<float4>(P, P->off_dwtab);
+  a.ring = at<float4>(P, P->off_ring);
+  a.stride = P->stride;
+  a.R = P->R;
+  a.etabC = t;
+  a.phitab = t + p.nt;
+  a.rowscal = t + p.nt + P->nphi;
+  a.detab = t + 3 * p.nt + P->nphi;
+  a.partials = at<double>(P, P->off_partials);
+  a.snaps = P->nsnap ? at<double2>(P, P->off_snaps) : nullptr;
+  a.colsplit = at<int64_t>(P, P->off_colsplit);
+  int* deps = at<int>(P, P->off_deps);
+  a.dep_off = deps;
+  a.rd_off = deps + P->grid + 1;
+  a.dep = reinterpret_cast<const int2*>(deps + 2 * (P->grid + 1));
+  a.rd = deps + 2 * (P->grid + 1) + 2 * fdtd::kDwMaxDeps;
+  a.done = at<unsigned long long>(P, P->off_done);
+  a.sync = at<fdtd::SyncWords>(P, P->off_sync);
+  a.nx = p.nx;
+  a.nt = p.nt;
+  a.nphi = P->nphi;
+  a.D = p.D;
+  a.tstep = p.tstep;
+  a.kfix = P->kfix;
+  a.khalo = P->khalo;
+  a.hreuse = P->march_smem > 0 ? 1 : 0;
+  a.mid_weight = P->mid_weight;
+  auto split = [](cd v) {
+    const float rh = (float)v.re, ih = (float)v.im;
+    return make_float4(rh, ih, (float)(v.re - (double)rh), (float)(v.im - (double)ih));
+  };
+  a.d1 = split(cd{P->c1.re - 1.0, P->c1.im});
+  a.c2 = split(P->c2);
+  a.c3 = split(P->c3);
+  a.gs = split(P->gs);
+  cd pw = cd{1.0, 0.0};
+  for (int k = 0; k <= fdtd::kMaxTrunc; ++k) {
+    a.c2pow[k] = split(pw);
+    pw = pw * P->c2;
+  }
+  a.spin_cycles = p.spin_cycles > 0 ? p.spin_cycles : 4000000000LL;  // default ~2 s at 2 GHz
+  if (P->n_probes > 0) {
+    ProbeView v = probe_view(P);
+    a.probe_off = v.off;
+    a.probe_col = v.col;
+    a.probe_idx = v.idx;
+    a.probe_val = v.val;
+  }
+  const int64_t per = P->rows_per_launch;
+  for (int64_t n0 = P->rows_done; n0 < end; n0 += per) {
+    a.n_begin = n0;
+    a.n_end = (n0 + per < end) ? n0 + per : end;
+    cudaError_t e = fdtd::launch_march_dw(a, P->grid, P->march_smem, P->stream);
+    if (e == cudaSuccess)
+      e = fdtd::launch_norms_dw(a.partials, P->grid, a.n_begin, a.n_end, at<cd>(P, P->off_etab),
+                                at<cd>(P, P->off_phi), P->C, p.delta, at<double>(P, P->off_norms), P->stream);
+    if (e != cudaSuccess) return cuda_fail(P, e, "double-float march launch");
+  }
+  P->rows_done = end;
+  return FDTD_OK;
+}
+
 fdtd_status fdtd_march(fdtd_plan_t P, int64_t n_rows) {
   if (!P) return FDTD_ERR_INVALID_ARG;
   if (P->state < 2) return fail(P, FDTD_ERR_STATE, "fdtd_march before fdtd_set_boundary");
@@ -272,6 +512,7 @@ fdtd_status fdtd_march(fdtd_plan_t P, int64_t n_rows) {
   int64_t end = P->rows_done + n_rows;
   if (end > p.nt) end = p.nt;
   if (end <= P->rows_done) return FDTD_OK;
+  if (P->dw) return march_dw(P, end);
   fdtd::MarchArgs a;
   memset(&a, 0, sizeof a);
   a.ring = at<cd>(P, P->off_ring);
@@ -303,7 +544,14 @@ fdtd_status fdtd_march(fdtd_plan_t P, int64_t n_rows) {
   a.mid_weight = P->mid_weight;
   a.c2pow[0] = cd{1.0, 0.0};
   for (int k = 1; k <= fdtd::kMaxTrunc; ++k) a.c2pow[k] = a.c2pow[k - 1] * P->c2;
-  a.spin_cycles = 4000000000LL;  // ~2 s at 2 GHz
+  a.spin_cycles = p.spin_cycles > 0 ? p.spin_cycles : 4000000000LL;  // default ~2 s at 2 GHz
+  if (P->n_probes > 0) {
+    ProbeView v = probe_view(P);
+    a.probe_off = v.off;
+    a.probe_col = v.col;
+    a.probe_idx = v.idx;
+    a.probe_val = v.val;
+  }
   const int64_t per = p.rows_per_launch > 0 ? p.rows_per_launch : 4096;
   for (int64_t n0 = P->rows_done; n0 < end; n0 += per) {
     a.n_begin = n0;
@@ -329,6 +577,14 @@ int64_t fdtd_readout_bytes(fdtd_plan_t P, int32_t kind) {
     }
     case FDTD_READ_ETABLE: return (int64_t)sizeof(cd) * p.nt;
     case FDTD_READ_ROWS_DONE: return (int64_t)sizeof(int64_t);
+    case FDTD_READ_STATE: return state_bytes(P, 0);
+    case FDTD_READ_PROBES: return (int64_t)sizeof(cd) * P->n_probes;
+    case FDTD_READ_MEASURES: {
+      if (p.init_cond != FDTD_IC_STIM_EMISSION || !P->nsnap) return -1;
+      if (P->rows_done == 0) return 0;
+      int64_t ns = (P->rows_done - 1) / (p.tstep + 1) + 1;
+      return (int64_t)(4 * sizeof(double)) * ns;
+    }
   }
   return -1;
 }
@@ -338,6 +594,8 @@ fdtd_status fdtd_readout(fdtd_plan_t P, int32_t kind, void* dst, int64_t dst_byt
   if (P->state < 2) return fail(P, FDTD_ERR_STATE, "fdtd_readout before fdtd_set_boundary");
   if (P->batched) return batch_readout(P, 0, kind, dst, dst_bytes);
   int64_t need = fdtd_readout_bytes(P, kind);
+  if (need < 0 && kind == FDTD_READ_MEASURES)
+    return fail(P, FDTD_ERR_INVALID_ARG, "measures need a stimulated-emission plan with snapshots (tstep >= 0)");
   if (need < 0) return fail(P, FDTD_ERR_INVALID_ARG, "unknown readout kind");
   if (!dst || dst_bytes < need) return fail(P, FDTD_ERR_INVALID_ARG, "readout destination missing or too small");
   cudaError_t e = cudaStreamSynchronize(P->stream);
@@ -354,11 +612,31 @@ fdtd_status fdtd_readout(fdtd_plan_t P, int32_t kind, void* dst, int64_t dst_byt
   const fdtd_params& p = P->p;
   const void* src = nullptr;
   switch (kind) {
-    case FDTD_READ_ROW: src = P->ws + P->off_ring + P->elem * (size_t)((P->rows_done - 1) % P->R) * P->stride; break;
+    case FDTD_READ_ROW:
+      src = P->ws + P->off_ring + P->elem * (size_t)((P->rows_done - 1) % P->R) * P->stride;
+      if (P->dw) {  // double-float pairs -> complex128
+        e = fdtd::launch_row_dw(static_cast<const float4*>(src), p.nx, at<double2>(P, P->off_rowout), P->stream);
+        if (e != cudaSuccess) return cuda_fail(P, e, "row conversion");
+        src = P->ws + P->off_rowout;
+      }
+      break;
     case FDTD_READ_NORMS: src = P->ws + P->off_norms; break;
     case FDTD_READ_SNAPSHOTS: src = P->ws + P->off_snaps; break;
     case FDTD_READ_ETABLE: src = P->ws + P->off_etab; break;
     case FDTD_READ_ROWS_DONE: memcpy(dst, &P->rows_done, sizeof(int64_t)); return FDTD_OK;
+    case FDTD_READ_STATE: {
+      fdtd_status st = state_readout(P, 0, dst, dst_bytes, P->stream);
+      return st == FDTD_OK ? FDTD_OK : fail(P, st, "checkpoint copy");
+    }
+    case FDTD_READ_PROBES: src = probe_view(P).val; break;
+    case FDTD_READ_MEASURES:
+      e = fdtd::launch_measures(at<cd>(P, P->off_snaps), p.nx, p.tstep, need / (int64_t)(4 * sizeof(double)),
+                                at<cd>(P, P->off_etab), at<cd>(P, P->off_e0tab), at<cd>(P, P->off_phi),
+                                at<double>(P, P->off_norms), p.D, p.delta, p.gamma, p.alpha,
+                                at<double>(P, P->off_meas), P->stream);
+      if (e != cudaSuccess) return cuda_fail(P, e, "measures kernel");
+      src = P->ws + P->off_meas;
+      break;
   }
   if (need > 0) {
     e = cudaMemcpyAsync(dst, src, (size_t)need, cudaMemcpyDefault, P->stream);

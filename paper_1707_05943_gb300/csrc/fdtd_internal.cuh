@@ -47,6 +47,12 @@ constexpr int kF32P = 8;             // leading columns of a segment kept in reg
 constexpr int kF32MaxTrunc = 16;     // |c2|^16 < 2^-26 required (|c2| < 0.32)
 constexpr int kClusterMax = 16;      // CTAs per cluster at most
 
+// double-float march (march_dw.cu)
+constexpr int kDwThreads = 512;      // threads per CTA
+constexpr int kDwP = 4;              // leading columns of a segment kept in registers
+constexpr int kDwSlack = 32;         // ring rows beyond D+2: how far a CTA may run ahead of its readers
+constexpr int kDwMaxDeps = 4096;     // (cta, lag) entries of the dependency lists, all CTAs together
+
 // sync words at the start of the workspace
 struct SyncWords {
   unsigned int bar_count;
@@ -84,6 +90,44 @@ struct MarchArgs {
   int mid_weight;        // cost of a column of -a < x <= 3a in bulk columns
   cd c2pow[kMaxTrunc + 1];  // c2^0 .. c2^kMaxTrunc
   long long spin_cycles; // bounded wait of the grid barrier
+  // probes: points of row n are probe_col[probe_off[n] .. probe_off[n+1]) (null: none);
+  // the value of column probe_col[k] goes to probe_val[probe_idx[k]]
+  const int* probe_off;
+  const int* probe_col;
+  const int* probe_idx;
+  double2* probe_val;
+};
+
+// ---------------------------------------------------------------- double-float march args
+// A complex value in double-float: (rh + rl) + i (ih + il), stored as float4
+// (rh, ih, rl, il); |rl| <= ulp(rh)/2 once normalised.
+struct DwArgs {
+  float4* ring;          // R rows x stride, R = D + 2 + kDwSlack
+  int64_t stride;
+  int R;
+  const float4* etabC;   // C e(r delta), r < nt
+  const float4* phitab;  // phi(-a - j delta), j < nphi
+  const float4* rowscal; // R1(n), R2(n)
+  const float4* detab;   // E(i-D) - E(i), i < nt + D
+  double* partials;      // (n - n_begin) * grid + cta: sum over the CTA's columns of w_j |psi|^2
+  double2* snaps;        // complex128 snapshots or null
+  const int64_t* colsplit;
+  const int* dep_off;    // grid+1: CTA b's dependencies are dep[dep_off[b] .. dep_off[b+1])
+  const int2* dep;       // (cta, lag): row n of this CTA needs row n - lag of `cta` complete
+  const int* rd_off;     // grid+1: CTA b's readers are rd[rd_off[b] .. rd_off[b+1])
+  const int* rd;
+  unsigned long long* done;  // per CTA: rows completed (absolute row index + 1)
+  SyncWords* sync;
+  int64_t n_begin, n_end;
+  int64_t nx, nt, nphi;
+  int D, tstep, kfix, khalo, hreuse, mid_weight;
+  float4 d1, c2, c3, gs;  // c1 - 1, c2, c3, -(Gamma/4)/A in double-float
+  float4 c2pow[kMaxTrunc + 1];
+  long long spin_cycles;
+  const int* probe_off;  // as in MarchArgs
+  const int* probe_col;
+  const int* probe_idx;
+  double2* probe_val;
 };
 
 // ---------------------------------------------------------------- boundary args
@@ -109,7 +153,11 @@ struct InstDesc {
   int64_t smem_cols;       // pair-sum columns per CTA that fit the launch's shared memory
   int D, R, kfix, khalo, mid_weight, tstep;
   float2 d1, c2, c3, gs;   // c1 - 1, c2, c3, -(Gamma/4)/A
+  float2 d1lo, c2lo, c3lo; // their FP32 rounding errors: d1 = d1 + d1lo to ~2^-48 (a coefficient
+                           // error is the same at every step, so it would grow linearly along
+                           // a characteristic)
   float2 c2pow[kF32MaxTrunc + 1];
+  float2 c2powlo[kF32MaxTrunc + 1];
   double C, delta;
   float2* ring;            // R rows x stride complex64
   float2* snaps;           // or null
@@ -171,6 +219,15 @@ struct fdtd_plan_s {
   size_t march_smem;     // dynamic shared memory of the march (delay pair sums)
   int mid_weight;        // column split weight of -a < x <= 3a
   bool record_errors = true;  // false: keep no message (no host allocation on error paths)
+  // FDTD_F64_DW plans
+  bool dw = false;
+  size_t off_dwtab = 0, off_done = 0, off_deps = 0, off_rowout = 0;
+  // stimulated-emission plans: one-excitation e0 table and the App. D measures
+  size_t off_e0tab = 0, off_meas = 0;
+  // probes (fdtd_set_probes)
+  size_t off_probes = 0;
+  int64_t n_probes = 0;
+  int64_t rows_per_launch = 0;
   // complex64 (batched) plans
   bool batched = false;
   std::vector<fdtd_batch_inst> inst;
@@ -191,6 +248,11 @@ struct fdtd_plan_s {
     if (cap_stream) cudaStreamDestroy(cap_stream);
   }
 };
+
+// checkpoint / resume (state.cu)
+int64_t state_bytes(fdtd_plan_s* P, int inst);
+fdtd_status state_readout(fdtd_plan_s* P, int inst, void* dst, int64_t dst_bytes, cudaStream_t s);
+fdtd_status state_restore(fdtd_plan_s* P, const void* blob, int64_t nbytes, cudaStream_t s, int64_t* rows_restored);
 
 // fills a plan without allocating it (fdtd_plan = new + this)
 fdtd_status fdtd_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n_instances, void* cuda_stream,
@@ -218,6 +280,10 @@ cudaError_t launch_boundary_pre(const BoundaryArgs& a, cudaStream_t s);
 cudaError_t launch_etable_batch(const EtabArgs* dev_args, int n, int64_t max_nt, cudaStream_t s);
 cudaError_t launch_boundary_post(const BoundaryArgs& a, cudaStream_t s);
 cudaError_t launch_gamma_star(const int32_t* n, const double* z, double* out, int64_t count, cudaStream_t s);
+cudaError_t launch_etable_e0(const BoundaryArgs& a, cd* e0tab, cd* hscratch, cudaStream_t s);
+cudaError_t launch_measures(const cd* snaps, int64_t nx, int tstep, int64_t nsnap, const cd* e1tab, const cd* e0tab,
+                            const cd* phitab, const double* norms, int D, double delta, double gamma, double alpha,
+                            double* out, cudaStream_t s);
 cudaError_t launch_march_f64(const MarchArgs& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_tables32(const InstDesc& I, const cd* detab, const cd* rowscal, cudaStream_t s);
 cudaError_t launch_advance(InstDesc* insts, int ninst, int64_t rows, cudaStream_t s);
@@ -226,4 +292,12 @@ int march_f32c_max_clusters(int csize, size_t smem);
 cudaError_t launch_march_f32c(const InstDesc* insts, const WorkItem* items, int nitems, unsigned int* queue,
                               SyncWords* sync, int nclusters, int csize, size_t smem, cudaStream_t s);
 int march_f64_max_grid(int device);
+int march_dw_max_grid(int device);
+cudaError_t launch_tables_dw(const cd* etab, const cd* phitab, const cd* rowscal, const cd* detab, double C,
+                             int64_t nt, int64_t nphi, int D, float4* etabC, float4* phitab_dw, float4* rowscal_dw,
+                             float4* detab_dw, cudaStream_t s);
+cudaError_t launch_march_dw(const DwArgs& a, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_norms_dw(const double* partials, int grid, int64_t n_begin, int64_t n_end, const cd* etab,
+                            const cd* phitab, double C, double delta, double* norms, cudaStream_t s);
+cudaError_t launch_row_dw(const float4* src, int64_t nx, double2* dst, cudaStream_t s);
 }  // namespace fdtd

@@ -123,7 +123,14 @@ __device__ __noinline__ float2 rhs_general32(const InstDesc& I, int64_t n, int n
   *a_hi = v[0];
   float2 S = mulc(I.d1, v[0]);
   S = fmac(I.c2, v[1], S);
-  if (dl) S = fmac(I.c3, add(add(v[2], v[3]), add(v[4], v[5])), S);
+  float2 L = mulc(I.d1lo, v[0]);  // the coefficients' low parts
+  L = fmac(I.c2lo, v[1], L);
+  if (dl) {
+    const float2 sq = add(add(v[2], v[3]), add(v[4], v[5]));
+    S = fmac(I.c3, sq, S);
+    L = fmac(I.c3lo, sq, L);
+  }
+  S = add(S, L);
   if (s2) {
     const float w = (r2 == 0) ? 0.5f : 1.0f;
     S = fmac(I.gs, scal(w, sub(add(v[6], v[7]), add(v[8], v[9]))), S);
@@ -140,16 +147,21 @@ __device__ __forceinline__ float2 rhs_bulk32(const InstDesc& I, const RowF& R, i
   const int D = I.D;
   float2 a = ldr(R.row1 + j - 1);
   *a_hi = a;
+  const float2 b = ldr(R.row1 + j);
   float2 S = mulc(I.d1, a);
-  S = fmac(I.c2, ldr(R.row1 + j), S);
+  S = fmac(I.c2, b, S);
+  float2 L = fmac(I.c2lo, b, mulc(I.d1lo, a));
   if (R.rowD) {
     float2 hn = add(ldr(R.rowD + j - D - 1), ldr(R.rowD + j - D));
     if (R.rowD1) {
       float2 hp = (R.hs && !R.cold) ? R.hs[j - R.hbase] : add(ldr(R.rowD1 + j - D - 1), ldr(R.rowD1 + j - D));
-      S = fmac(I.c3, add(hn, hp), S);
+      const float2 sq = add(hn, hp);
+      S = fmac(I.c3, sq, S);
+      L = fmac(I.c3lo, sq, L);
     }
     if (R.hs) R.hs[j - R.hbase] = hn;
   }
+  S = add(S, L);
   const int64_t i = R.n - j - 1 + D;  // r2 + D
   if (i >= 0) {
     S = fmac(R.R1, I.detab32[i], S);
@@ -371,7 +383,7 @@ __global__ void __launch_bounds__(kF32Threads, 1)
           __syncwarp();
           if (tid == 0) {
             float2 yh = (h0 == 0) ? I.bnd32[2 * n] : f2(0.f, 0.f);
-            for (int c = 0; c < nh; ++c) yh = fmac(I.c2, yh, s_halo[c]);
+            for (int c = 0; c < nh; ++c) yh = fmac(I.c2lo, yh, fmac(I.c2, yh, s_halo[c]));
             s_carry[0] = yh;
           }
         }
@@ -488,7 +500,7 @@ __global__ void __launch_bounds__(kF32Threads, 1)
               float2 S = rhs_general32(I, n, R.nslot, j, R.R2, &ah);
               if (j == 0) ah = I.bnd32[2 * (n - 1)];
               S = add(S, __ldcg(es_rd + j));
-              emit(j, ah, fmac(I.c2, y, S));
+              emit(j, ah, fmac(I.c2lo, y, fmac(I.c2, y, S)));
             }
           } else {
             // block-relative 32-bit offsets: column j = c0 + k
@@ -505,21 +517,28 @@ __global__ void __launch_bounds__(kF32Threads, 1)
             const int k0 = (int)(t0 - c0), k1 = (int)(t1 - c0);
             const int klast = (int)(I.nx - 1 - c0);
             const float2 d1c = I.d1, c2c = I.c2, c3c = I.c3, R1 = R.R1, R2 = R.R2;
+            const float2 d1l = I.d1lo, c2l = I.c2lo, c3l = I.c3lo;
             const int kfix = I.kfix;
             for (int k = k0; k < k1; ++k) {
               const float2 a = a1s[k], b = a1s[k + 1];
               float2 S = mulc(d1c, a);
               S = fmac(c2c, b, S);
+              float2 L = fmac(c2l, b, mulc(d1l, a));
               if (dd) {
                 const float2 hn = add(ads[k], ads[k + 1]);
-                if (d1) S = fmac(c3c, add(hn, use_hs ? hsb[k] : add(ad1s[k], ad1s[k + 1])), S);
+                if (d1) {
+                  const float2 sq = add(hn, use_hs ? hsb[k] : add(ad1s[k], ad1s[k + 1]));
+                  S = fmac(c3c, sq, S);
+                  L = fmac(c3l, sq, L);
+                }
                 if (hsb) hsb[k] = hn;
               }
+              S = add(S, L);
               const int i = kde - k;
               if (i >= 0) S = fmac(R1, des[i], S);
               if (i >= D) S = fmac(R2, phs[i - D], S);
               S = add(S, los[k]);
-              S = fmac(c2c, y, S);
+              S = fmac(c2l, y, fmac(c2c, y, S));
               if (v < kfix) {
                 o_hi[k] = S;
                 o_e[k] = a;
@@ -565,7 +584,7 @@ __global__ void __launch_bounds__(kF32Threads, 1)
 #pragma unroll 4
             for (int u = 0; u < nf; ++u) {  // only the kfix parked columns take the carry
               const int k = kb + u;
-              const float2 S = fmac(I.c2pow[u + 1], carry, oh[k]);
+              const float2 S = fmac(I.c2powlo[u + 1], carry, fmac(I.c2pow[u + 1], carry, oh[k]));
               const float2 A = oe[k];
               float2 sv, e;
               two_sum(A.x, S.x, sv.x, e.x);

@@ -339,6 +339,17 @@ __global__ void __launch_bounds__(kMarchThreads, 1) k_march_f64(const MarchArgs 
       if (j_hi == A.nx && j_lo < j_hi) t -= 0.5 * cabs2(ldcg(R.row0 + A.nx - 1));  // trapezoid end weight
       A.partials[(n & 1) * gridDim.x + blockIdx.x] = t;
     }
+    // probes of row n in this CTA's columns (its stores of row n are complete)
+    if (A.probe_off && tid < 32) {
+      const int k1 = A.probe_off[n + 1];
+      for (int k = A.probe_off[n] + tid; k < k1; k += 32) {
+        const int j = A.probe_col[k];
+        if (j >= j_lo && j < j_hi) {
+          const cd v = ldcg(R.row0 + j);
+          A.probe_val[A.probe_idx[k]] = make_double2(v.re, v.im);
+        }
+      }
+    }
     if (!grid_barrier(A.sync, A.spin_cycles, n)) return;
     if (blockIdx.x == 0 && tid == 0) {
       const double* pp = A.partials + (n & 1) * gridDim.x;

@@ -174,7 +174,7 @@ __device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* map, int
 __global__ void __launch_bounds__(128) k_gemm_nt_tma(const NtArgs g, const __grid_constant__ CUtensorMap tmA,
                                                      const __grid_constant__ CUtensorMap tmB) {
   extern __shared__ unsigned char dsmem[];
-  __shared__ __align__(8) uint64_t full[kTmaStages], empty[kTmaStages];
+  __shared__ __align__(8) uint64_t full[kTmaStages], empty[kTmaStages], drain;
   __shared__ uint32_t tmem_sh;
   __shared__ int abort_sh;
   unsigned char* sbase = (unsigned char*)(((uintptr_t)dsmem + 1023) & ~(uintptr_t)1023);
@@ -192,6 +192,7 @@ __global__ void __launch_bounds__(128) k_gemm_nt_tma(const NtArgs g, const __gri
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&full[s])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&empty[s])));
     }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&drain)));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     abort_sh = 0;
   }
@@ -263,6 +264,16 @@ __global__ void __launch_bounds__(128) k_gemm_nt_tma(const NtArgs g, const __gri
       atomicExch(&g_mlp_status, 1);
       abort_sh = 1;
     }
+  }
+  __syncthreads();
+  if (abort_sh && tid == 0) {
+    // a wait gave up: MMAs committed earlier may still be reading the stages and
+    // writing tensor memory.  One more commit (it tracks every MMA this thread
+    // issued) on a spare barrier, waited on with the same bound, lets them
+    // finish before the tensor memory is released and the CTA leaves.
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(su32(&drain))
+                 : "memory");
+    mbar_wait(su32(&drain), 0u, g.spin);
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");

@@ -23,16 +23,17 @@ LIB_PATH = os.path.join(_PKG, "_build", "libfdtd.so")
 # fdtd_status
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_BOUNDS, ERR_NOT_CONVERGED, \
     ERR_STATE = range(9)
-F64, F32_COMP = 0, 1
+F64, F32_COMP, F64_DW = 0, 1, 2
 IC_STIM_EMISSION, IC_TWO_PHOTON_EXP, IC_TWO_PHOTON_GAUSS = 2, 3, 4
-BOUNDARY_ANALYTIC, BOUNDARY_TABLE = 0, 1
-READ_ROW, READ_NORMS, READ_SNAPSHOTS, READ_ETABLE, READ_ROWS_DONE = range(5)
+BOUNDARY_ANALYTIC, BOUNDARY_TABLE, BOUNDARY_RESTORE = 0, 1, 2
+READ_ROW, READ_NORMS, READ_SNAPSHOTS, READ_ETABLE, READ_ROWS_DONE, READ_MEASURES, READ_STATE, READ_PROBES = range(8)
 
 EXPORTS = ["fdtd_plan", "fdtd_bind_workspace", "fdtd_set_boundary", "fdtd_march", "fdtd_readout",
            "fdtd_readout_bytes", "fdtd_destroy", "fdtd_status_string", "fdtd_last_error", "fdtd_gamma_star",
            "fdtd_march_noalloc", "fdtd_noalloc_max_bytes", "fdtd_readout_instance", "fdtd_readout_instance_bytes",
            "fdtd_mlp_param_count", "fdtd_mlp_workspace_bytes", "fdtd_mlp_sync_bf16", "fdtd_mlp_forward",
-           "fdtd_mlp_train_step", "fdtd_gemm_bf16", "fdtd_mlp_status", "fdtd_march_graph"]
+           "fdtd_mlp_train_step", "fdtd_gemm_bf16", "fdtd_mlp_status", "fdtd_march_graph", "fdtd_alu_probe",
+           "fdtd_geometric_measure", "fdtd_set_probes"]
 
 
 class FdtdParams(ctypes.Structure):
@@ -54,6 +55,8 @@ class FdtdParams(ctypes.Structure):
         ("rows_per_launch", ctypes.c_int32),
         ("cluster_ctas", ctypes.c_int32),
         ("mid_weight", ctypes.c_int32),
+        ("max_probes", ctypes.c_int64),
+        ("spin_cycles", ctypes.c_int64),
     ]
 
 
@@ -116,10 +119,14 @@ def lib() -> ctypes.CDLL:
         L.fdtd_mlp_train_step.argtypes = [mp, vp, vp, i32, ctypes.c_float, i32, vp, vp, vp]
         L.fdtd_gemm_bf16.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, vp]
         L.fdtd_mlp_status.argtypes = [vp]
+        L.fdtd_alu_probe.argtypes = [i32, vp, ctypes.POINTER(ctypes.c_double)]
+        L.fdtd_geometric_measure.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_double)]
+        L.fdtd_set_probes.argtypes = [vp, vp, i64]
         for f in ("fdtd_plan", "fdtd_bind_workspace", "fdtd_set_boundary", "fdtd_march", "fdtd_readout",
                   "fdtd_gamma_star", "fdtd_march_noalloc", "fdtd_readout_instance", "fdtd_mlp_param_count",
                   "fdtd_mlp_workspace_bytes", "fdtd_mlp_sync_bf16", "fdtd_mlp_forward", "fdtd_mlp_train_step",
-                  "fdtd_gemm_bf16", "fdtd_mlp_status", "fdtd_march_graph"):
+                  "fdtd_gemm_bf16", "fdtd_mlp_status", "fdtd_march_graph", "fdtd_alu_probe",
+                  "fdtd_geometric_measure", "fdtd_set_probes"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -158,6 +165,12 @@ def fdtd_set_boundary(plan, source: int = BOUNDARY_ANALYTIC, device_table: int =
 
 def fdtd_march(plan, n_rows: int):
     _check(lib().fdtd_march(plan, n_rows), plan, "fdtd_march")
+
+
+def fdtd_set_probes(plan, points):
+    """points: (count, 2) int64 array of (row n, column index j)."""
+    a = np.ascontiguousarray(points, dtype=np.int64).reshape(-1, 2)
+    _check(lib().fdtd_set_probes(plan, a.ctypes.data, a.shape[0]), plan, "fdtd_set_probes")
 
 
 def fdtd_march_graph(plan, n_rows: int):
@@ -235,6 +248,21 @@ def fdtd_gemm_bf16(a_ptr: int, b_ptr: int, c_ptr: int, M: int, N: int, K: int, l
                                 ldb, ctypes.c_void_p(stream or 0)), None, "fdtd_gemm_bf16")
 
 
+def fdtd_alu_probe(kind: int, stream: int | None = None) -> float:
+    """Measured FMA throughput in flop/s: kind 0 FP64, 1 FP32, 2 packed FP32 pairs."""
+    v = ctypes.c_double()
+    _check(lib().fdtd_alu_probe(kind, ctypes.c_void_p(stream or 0), ctypes.byref(v)), None, "fdtd_alu_probe")
+    return v.value
+
+
+def fdtd_geometric_measure(det_m) -> float:
+    """N_geo of App. D from a host array of det M samples (library host code)."""
+    a = np.ascontiguousarray(det_m, dtype=np.float64)
+    v = ctypes.c_double()
+    _check(lib().fdtd_geometric_measure(a.ctypes.data, a.shape[0], ctypes.byref(v)), None, "fdtd_geometric_measure")
+    return v.value
+
+
 def fdtd_mlp_status(stream: int | None = None):
     _check(lib().fdtd_mlp_status(ctypes.c_void_p(stream or 0)), None, "fdtd_mlp_status")
 
@@ -260,6 +288,8 @@ class Config:
     rows_per_launch: int = 0
     cluster_ctas: int = 0
     mid_weight: int = 0
+    max_probes: int = 0
+    spin_cycles: int = 0
 
     def c(self) -> FdtdParams:
         p = FdtdParams()
@@ -292,13 +322,22 @@ class Solver:
 
     @property
     def cdtype(self):
-        return np.complex128 if self.cfg.precision == F64 else np.complex64
+        return np.complex64 if self.cfg.precision == F32_COMP else np.complex128
 
     def set_boundary(self, table=None):
         if table is None:
             fdtd_set_boundary(self.plan, BOUNDARY_ANALYTIC, 0, 0)
         else:
             fdtd_set_boundary(self.plan, BOUNDARY_TABLE, table.data_ptr(), self.cfg.nt)
+
+    def checkpoint(self) -> np.ndarray:
+        """FDTD_READ_STATE into host memory."""
+        return self.read(READ_STATE)
+
+    def restore(self, state: np.ndarray):
+        """FDTD_BOUNDARY_RESTORE from a checkpoint in host memory."""
+        st = np.ascontiguousarray(state, dtype=np.uint8)
+        fdtd_set_boundary(self.plan, BOUNDARY_RESTORE, st.ctypes.data, st.nbytes)
 
     def march(self, n_rows: int):
         fdtd_march(self.plan, n_rows)
@@ -310,12 +349,17 @@ class Solver:
             fdtd_readout(self.plan, kind, out.data_ptr(), out.numel() * out.element_size())
             return out
         if dtype is None:
-            dtype = {READ_NORMS: np.float64, READ_ETABLE: np.complex128, READ_ROWS_DONE: np.int64}.get(kind,
-                                                                                                     self.cdtype)
+            dtype = {READ_NORMS: np.float64, READ_ETABLE: np.complex128, READ_ROWS_DONE: np.int64,
+                     READ_MEASURES: np.float64, READ_STATE: np.uint8,
+                     READ_PROBES: np.complex128}.get(kind, self.cdtype)
         arr = np.empty(max(nbytes, 0) // np.dtype(dtype).itemsize, dtype=dtype)
         if nbytes > 0:
             fdtd_readout(self.plan, kind, arr.ctypes.data, arr.nbytes)
         return arr
+
+    def measures(self):
+        """App. D: (Re mu, Im mu, lambda, det M) per snapshot row (stimulated emission)."""
+        return self.read(READ_MEASURES).reshape(-1, 4)
 
     def snapshots(self):
         a = self.read(READ_SNAPSHOTS)
@@ -331,3 +375,4 @@ class Solver:
             self.close()
         except Exception:
             pass
+

@@ -2,17 +2,24 @@
 on outputs the oracle can compute.
 
 * The large FP64 instance (2^20 marched columns, D = 2000, Gaussian pair),
-  marched in 4096-row launches for a prefix of 6145 rows (past the delay
-  onset at row D + 1 and across a launch boundary): the oracle marches a
-  narrow box of the first D + 512 columns, which is exact there because a
-  column only reads columns to its left and the exact boundary; every stored
-  row must match it to 1e-12 relative L2.  Beyond the box, a property that
-  holds at any width: nothing reaches past the light cone x = t + a of the
-  mirror source (on row n, columns beyond n + D + 400 are exactly zero: the
-  row recurrence's tail |c2|^d underflows well within 400 columns).
+  in FDTD_F64 and in FDTD_F64_DW, marched in 4096-row launches for a prefix of 12289 rows (past the delay
+  onset at row D + 1 and across two launch boundaries).  The oracle marches a
+  box of the first 16384 columns, which is exact there because a column reads
+  only columns to its left, mirror columns of -a < x <= a and the exact
+  boundary.  The box covers the cost-split CTAs of -a < x <= 3a, the CTA that
+  holds the boundary between the two kinds of columns, and the first two CTAs
+  that march nothing but bulk columns x > 3a (their columns start near 5639
+  and 12932 at 152 CTAs); the light cone x = t + a reaches column ~14300 by
+  the last row, so their values are non-zero.  Every stored row must match to
+  1e-12 relative L2.  Beyond the box, a property that holds at any width:
+  nothing reaches past the light cone of the mirror source (on row n, columns
+  beyond n + D + 400 are exactly zero: the row recurrence's tail |c2|^d
+  underflows well within 400 columns).
 * The seeded 256-instance complex64 batch (34 GB of rings, one plan, one
   persistent launch per 4096 rows): its three smallest instances against the
-  oracle over every stored row, 1e-6 relative L2.
+  oracle over every stored row, and its three largest (up to 65536 x 65536,
+  D up to 2000) against the FP64 march of the same instance (itself held to
+  the oracle above) over ~512 stored rows each, all at 1e-6 relative L2.
 """
 import numpy as np
 import pytest
@@ -37,30 +44,54 @@ def oparams(O, w):
                     init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center)
 
 
-def test_large_fp64_prefix_full_width(F, oracle):
-    rows, tstep = 6145, 1023
-    w = W.LARGE.with_(nt=rows)
+LARGE_ROWS, LARGE_TSTEP, LARGE_BOX = 12289, 1023, 16384
+
+
+@pytest.fixture(scope="module")
+def large_oracle(oracle):
+    w = W.LARGE.with_(nt=LARGE_ROWS)
+    return oracle.march(oparams(oracle, w.with_(nx=LARGE_BOX)), tstep=LARGE_TSTEP)["snaps"]
+
+
+def march_large(F, precision):
+    w = W.LARGE.with_(nt=LARGE_ROWS)
     s = F.Solver(F.Config(nx=w.nx, nt=w.nt, D=w.D, delta=w.delta, gamma=w.gamma, omega0=w.omega0, k=w.k,
-                          init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center, tstep=tstep,
-                          rows_per_launch=4096))
+                          init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center,
+                          tstep=LARGE_TSTEP, rows_per_launch=4096, precision=precision))
     s.set_boundary()
-    s.march(rows)
-    snaps = s.snapshots()
+    s.march(w.nt)
+    snaps = s.snapshots().astype(np.complex128)
     s.close()
-    box = w.D + 512
-    r = oracle.march(oparams(oracle, w.with_(nx=box)), tstep=tstep)
-    ref = r["snaps"]
-    got = snaps[:, :box]
+    return w, snaps
+
+
+def check_large(w, snaps, ref, label):
+    got = snaps[:, :LARGE_BOX]
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-    print(f"large workload, {rows} rows x 2^20 columns: first {box} columns vs oracle rel L2 {err:.2e}")
-    assert err < 1e-12
+    # the part of the box marched by CTAs that hold only bulk columns (x > 3a)
+    bulk = slice(5639, LARGE_BOX)
+    berr = np.linalg.norm(got[:, bulk] - ref[:, bulk]) / np.linalg.norm(ref[:, bulk])
+    print(f"{label}: large workload, {w.nt} rows x 2^20 columns: first {LARGE_BOX} columns vs oracle "
+          f"rel L2 {err:.2e} (bulk-only CTAs {berr:.2e})")
+    assert np.linalg.norm(ref[:, bulk]) > 1e-3 * np.linalg.norm(ref)
+    assert err < 1e-12 and berr < 1e-12
     assert np.all(np.isfinite(snaps))
     for i in range(snaps.shape[0]):
-        n = i * (tstep + 1)
+        n = i * (LARGE_TSTEP + 1)
         # the sources reach x = t + a (line 3 of Eq. 1 switches on with theta(t - x + a)):
         # column n + D - 1 on row n; ahead of it the row recurrence leaves values that
         # shrink like |c2|^d with the distance d and underflow to zero well within 400 columns
         assert not np.any(snaps[i, n + w.D + 400:]), n
+
+
+def test_large_fp64_prefix_full_width(F, large_oracle):
+    w, snaps = march_large(F, F.F64)
+    check_large(w, snaps, large_oracle, "FP64")
+
+
+def test_large_double_float_prefix_full_width(F, large_oracle):
+    w, snaps = march_large(F, F.F64_DW)
+    check_large(w, snaps, large_oracle, "double-float")
 
 
 def test_seeded_batch_sampled_instances(F, oracle):
@@ -68,29 +99,51 @@ def test_seeded_batch_sampled_instances(F, oracle):
 
     import torch
     ws = W.batch(n=256)
-    pick = sorted(range(len(ws)), key=lambda i: ws[i].updates)[:3]
+    order = sorted(range(len(ws)), key=lambda i: ws[i].updates)
+    small, large = order[:3], order[-3:]
+    tsteps = {i: 0 for i in small}
+    tsteps.update({i: max(ws[i].nt // 512 - 1, 0) for i in large})
     cfgs = []
     for i, w in enumerate(ws):
         cfgs.append(F.Config(nx=w.nx, nt=w.nt, D=w.D, delta=w.delta, gamma=w.gamma, omega0=w.omega0, k=w.k,
                              init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center,
-                             tstep=0 if i in pick else -1, precision=F.F32_COMP).c())
+                             tstep=tsteps.get(i, -1), precision=F.F32_COMP).c())
     arr = (F.FdtdParams * len(ws))(*cfgs)
     nbytes, plan = ctypes.c_size_t(), ctypes.c_void_p()
     assert F.lib().fdtd_plan(arr, len(ws), None, ctypes.byref(nbytes), ctypes.byref(plan)) == F.OK
     buf = torch.empty(nbytes.value + 256, dtype=torch.uint8, device="cuda")
+    got = {}
     try:
         F.fdtd_bind_workspace(plan, (buf.data_ptr() + 255) // 256 * 256, nbytes.value)
         F.fdtd_set_boundary(plan)
         F.fdtd_march(plan, max(w.nt for w in ws))
-        for i in pick:
+        for i in small + large:
             w = ws[i]
             snaps = np.empty(F.fdtd_readout_instance_bytes(plan, i, F.READ_SNAPSHOTS) // 8, np.complex64)
             F.fdtd_readout_instance(plan, i, F.READ_SNAPSHOTS, snaps.ctypes.data, snaps.nbytes)
-            r = oracle.march(oparams(oracle, w), tstep=0)
-            got = snaps.reshape(-1, w.nx).astype(np.complex128)
-            err = np.linalg.norm(got - r["snaps"]) / np.linalg.norm(r["snaps"])
-            print(f"batch instance {i} ({w.nx} x {w.nt}, D {w.D}): rel L2 {err:.2e}")
-            assert err < 1e-6
+            norms = np.empty(w.nt, np.float64)
+            F.fdtd_readout_instance(plan, i, F.READ_NORMS, norms.ctypes.data, norms.nbytes)
+            got[i] = (snaps.reshape(-1, w.nx).astype(np.complex128), norms)
     finally:
         F.fdtd_destroy(plan)
         del buf
+    for i in small:
+        w = ws[i]
+        r = oracle.march(oparams(oracle, w), tstep=0)
+        err = np.linalg.norm(got[i][0] - r["snaps"]) / np.linalg.norm(r["snaps"])
+        print(f"batch instance {i} ({w.nx} x {w.nt}, D {w.D}) vs oracle: rel L2 {err:.2e}")
+        assert err < 1e-6
+    for i in large:
+        w = ws[i]
+        s = F.Solver(F.Config(nx=w.nx, nt=w.nt, D=w.D, delta=w.delta, gamma=w.gamma, omega0=w.omega0, k=w.k,
+                              init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center,
+                              tstep=tsteps[i]))
+        s.set_boundary()
+        s.march(w.nt)
+        ref, rn = s.snapshots(), s.read(F.READ_NORMS)
+        s.close()
+        err = np.linalg.norm(got[i][0] - ref) / np.linalg.norm(ref)
+        nerr = np.max(np.abs(got[i][1] - rn)) / np.max(rn)
+        print(f"batch instance {i} ({w.nx} x {w.nt}, D {w.D}) vs FP64 march: rel L2 {err:.2e} over "
+              f"{ref.shape[0]} stored rows, norms {nerr:.2e}")
+        assert err < 1e-6 and nerr < 1e-6

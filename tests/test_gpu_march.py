@@ -1,10 +1,12 @@
-"""GPU parity of the FP64 march (libfdtd through its C ABI) with the CPU oracle.
+"""GPU parity of the FP64-accurate marches (libfdtd through its C ABI) with the
+CPU oracle: FDTD_F64 (complex128) and FDTD_F64_DW (double-float pairs of FP32,
+48 significant bits), each held to the same bar.
 
-Tolerance: 1e-12 relative L2 over every stored row (FP64 rounding of two
+Tolerance: 1e-12 relative L2 over every stored row (rounding of two
 different evaluation orders: the march is stable, |xi| <= 1 (App. A), so the
 difference grows at most linearly in the ~1e4 steps along a characteristic;
-1e-12 leaves two orders of margin over 4096 x 1e-16).  e(t) tables: 1e-13
-relative to max |e|.
+1e-12 leaves two orders of margin over 4096 x 1e-16, and one over 4096 x
+2^-48 for the double-float march).  e(t) tables: 1e-13 relative to max |e|.
 """
 import math
 
@@ -76,58 +78,78 @@ def check_parity(F, oracle, w, **kw):
     return err
 
 
-def test_small_workload_full_grid(F, oracle):
+# FDTD_F64 and FDTD_F64_DW
+PREC = pytest.mark.parametrize("prec", [0, 2], ids=["f64", "dw"])
+
+
+@PREC
+def test_small_workload_full_grid(F, oracle, prec):
     # the 1024 x 4096, D = 40 two-photon exponential workload: every row compared
-    check_parity(F, oracle, W.SMALL)
+    check_parity(F, oracle, W.SMALL, precision=prec)
 
 
+@PREC
 @pytest.mark.parametrize("i", range(3))
-def test_jittered_two_photon(F, oracle, i):
+def test_jittered_two_photon(F, oracle, i, prec):
     # p = k - w0 + i Gamma (1-alpha)/2 != 0: gamma(n, z) at complex z
     w = W.jittered(W.exp_pair(512, 2048), seed=1707, n=3)[i]
-    check_parity(F, oracle, w)
+    check_parity(F, oracle, w, precision=prec)
 
 
-def test_stimulated_emission(F, oracle):
+@PREC
+def test_stimulated_emission(F, oracle, prec):
     w = W.Workload("stim", 512, 2048, 20, 0.1, 1.0, 2.3, 2.3, 2, alpha=0.5)
-    check_parity(F, oracle, w)
+    check_parity(F, oracle, w, precision=prec)
 
 
-def test_gaussian_pair(F, oracle):
+@PREC
+def test_gaussian_pair(F, oracle, prec):
     w = W.gauss_pair(600, 1500, D=40, a=1.0, gamma=1.0, k0a=0.3 * math.pi, sigma=1.0)
-    check_parity(F, oracle, w)
+    check_parity(F, oracle, w, precision=prec)
 
 
+@PREC
 @pytest.mark.parametrize("nx,nt,D", [(2, 40, 2), (40, 300, 40), (2048 + 7, 200, 10), (5, 1, 4), (6, 2, 6)])
-def test_edge_shapes(F, oracle, nx, nt, D):
+def test_edge_shapes(F, oracle, nx, nt, D, prec):
     # minimum box (nx = D), D = 2, a ragged chunk, only row 0, one marched row
     w = W.exp_pair(nx, nt, D=D, a=0.5 * D * 0.05)
-    check_parity(F, oracle, w)
+    check_parity(F, oracle, w, precision=prec)
 
 
-def test_many_ctas_ragged(F, oracle):
+@PREC
+def test_many_ctas_ragged(F, oracle, prec):
     # enough columns that every SM owns a range; nx not a multiple of anything
     w = W.exp_pair(20011, 360, D=40)
-    check_parity(F, oracle, w)
+    check_parity(F, oracle, w, precision=prec)
 
 
-def test_march_in_pieces_is_bitwise_equal(F):
+@PREC
+def test_many_ctas_wide_middle_region(F, oracle, prec):
+    # D large against a CTA's width: the mirror bars of -a < x <= 3a read columns of
+    # several CTAs, some to the right and up to D rows back; many launches
+    w = W.gauss_pair(24001, 1500, D=800, a=4.0, gamma=1.0, k0a=0.3 * math.pi, sigma=1.0, lead=4.0)
+    check_parity(F, oracle, w, precision=prec, rows_per_launch=333)
+
+
+@PREC
+def test_march_in_pieces_is_bitwise_equal(F, prec):
     w = W.exp_pair(3000, 700, D=40)
-    one = run_gpu(F, w)
-    pieces = run_gpu(F, w, pieces=[1, 250, 3, 1000])  # the last call is clamped at nt
+    one = run_gpu(F, w, precision=prec)
+    pieces = run_gpu(F, w, pieces=[1, 250, 3, 1000], precision=prec)  # the last call is clamped at nt
     assert np.array_equal(one["snaps"], pieces["snaps"])
     assert np.array_equal(one["norms"], pieces["norms"])
-    small = run_gpu(F, w, rows_per_launch=37)
+    small = run_gpu(F, w, rows_per_launch=37, precision=prec)
     assert np.array_equal(one["snaps"], small["snaps"])
 
 
-def test_boundary_table_source(F, oracle):
+@PREC
+def test_boundary_table_source(F, oracle, prec):
     # FDTD_BOUNDARY_TABLE: march from the oracle's e(t) instead of the kernel's
     import torch
     w = W.jittered(W.exp_pair(256, 900), seed=7, n=1)[0]
     et = oracle.etable(oparams(oracle, w), w.nt)
     t = torch.from_numpy(et.view(np.float64)).cuda()
-    s = F.Solver(cfg_of(F, w))
+    s = F.Solver(cfg_of(F, w, precision=prec))
     s.set_boundary(table=t)
     s.march(w.nt)
     g = s.snapshots()
@@ -182,3 +204,26 @@ def test_call_order_and_buffer_errors(F):
         assert np.all(np.isfinite(row))
     finally:
         F.fdtd_destroy(plan)
+
+
+@PREC
+def test_wait_timeout_latches_status(F, prec):
+    # a wait limit of one cycle: in FDTD_F64 every CTA that is not the last to reach
+    # a row's grid barrier gives up at once; in FDTD_F64_DW a CTA whose left
+    # neighbour has not yet published the previous row does.  Either latches
+    # FDTD_ERR_TIMEOUT and returns; no wait is left running, and the readout
+    # reports the status instead of data
+    import ctypes
+    w = W.exp_pair(20011, 64, D=40)
+    s = F.Solver(cfg_of(F, w, tstep=-1, spin_cycles=1, precision=prec))
+    s.set_boundary()
+    s.march(w.nt)
+    L = F.lib()
+    row = np.empty(w.nx, dtype=np.complex128)
+    st = L.fdtd_readout(s.plan, F.READ_ROW, ctypes.c_void_p(row.ctypes.data), row.nbytes)
+    assert st == F.ERR_TIMEOUT
+    assert b"row" in L.fdtd_last_error(s.plan)
+    # the context is still usable: a fresh plan with the default limit marches normally
+    s.close()
+    g = run_gpu(F, W.exp_pair(512, 200, D=40))
+    assert np.all(np.isfinite(g["snaps"]))

@@ -4,9 +4,10 @@
   the exact psi(x<-a,t) = C phi(x-t) e(t) at second order (this pins the
   square stencil, the delay term of App. A, the chi source and the boundary).
 * Two-excitation probability: int |psi|^2 dx + int int |chi|^2 = 1, with chi
-  rebuilt from the marched psi by Eq. 2.  This pins the mirror source terms
-  (lines 2-3 of Eq. 1), which validation test 1 does not reach: flipping the
-  sign of either one moves the total to ~4.6 or ~9.
+  rebuilt from the marched psi by Eq. 2 (the oracle's orc_chi).  This pins the
+  mirror source terms (lines 2-3 of Eq. 1), which validation test 1 does not
+  reach (flipping the sign of either one moves the total to ~4.6 or ~9), and
+  orc_chi itself: a wrong weight or sign of either term of Eq. 2 breaks the sum.
 * Causality: column m depends on nothing to the right of max(m, D/2), so a
   narrower box gives the same values on the common columns.
 * Stability (App. A): long runs stay bounded.
@@ -77,12 +78,16 @@ def total_probability(O, D, t_end=8.0, dk=0.0, alpha=1.0, Ltail=20.0):
     t = n * dl
     i = np.arange(int(np.floor((-a + t - Ltail) / dl)), n + Dh + 3)
     I1, I2 = np.meshgrid(i, i, indexing="ij")
+    pts = np.stack([I1.ravel(), I2.ravel(), np.full(I1.size, n)], axis=1)
+    chi = O.chi(p, grid, pts).reshape(I1.shape)
 
     def T(i1, i2):
         r1, r2 = n - i2 - Dh, n - i2 + Dh
         return psi(i1 - i2 - Dh, r1) * th(i2 + Dh) * th(r1) - psi(i1 - i2 + Dh, r2) * th(i2 - Dh) * th(r2)
 
-    chi = phiv((I1 - n) * dl) * phiv((I2 - n) * dl) - 0.5 * (T(I1, I2) + T(I2, I1))
+    # the same Eq. 2 written out here with numpy agrees (a check of the transcription)
+    chi_np = phiv((I1 - n) * dl) * phiv((I2 - n) * dl) - 0.5 * (T(I1, I2) + T(I2, I1))
+    assert np.max(np.abs(chi - chi_np)) <= 1e-13 * max(np.abs(chi_np).max(), 1e-300)
     w = np.ones(len(i))
     w[0] = w[-1] = 0.5
     p_chi = dl * dl * np.einsum("i,j,ij->", w, w, np.abs(chi) ** 2)
