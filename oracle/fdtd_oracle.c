@@ -16,6 +16,7 @@
  *                    Q, series for P, series for gamma*, and the expansion near
  *                    the negative real axis).
  *   orc_e_at         the two-level-system amplitude that drives the boundary:
+ *                    e0(t) of the two-photon plane wave (Sec. 2 (a)),
  *                    e1(t) of the stimulated-emission class (Sec. 2 (b)),
  *                    e0(t) of the two-photon exponential wavepacket (Sec. 2 (c),
  *                    Eq. for e(t) with p = k - w0 + i Gamma (1-alpha)/2), and
@@ -56,8 +57,9 @@ typedef struct {
   int64_t nx;        /* marched columns in x > -a: m = -D/2+1 .. -D/2+nx      */
   int64_t nt;        /* rows: t = n*delta, n = 0 .. nt-1                       */
   int32_t D;         /* 2a/delta (the paper's n_x), even, >= 2                 */
-  int32_t init_cond; /* 2: stimulated emission, 3: two identical exponential   */
-                     /* photons, 4: two identical Gaussian photons             */
+  int32_t init_cond; /* 1: two-photon plane wave, 2: stimulated emission,      */
+                     /* 3: two identical exponential photons, 4: two          */
+                     /* identical Gaussian photons                            */
   double delta;      /* grid step, dx = dt (Sec. 2)                           */
   double gamma;      /* decay rate Gamma                                      */
   double omega0;     /* two-level-system frequency                            */
@@ -204,11 +206,13 @@ static double half_a(const orc_params* p) { return 0.5 * p->D * p->delta; } /* a
 
 /* phi(x): Eq. for the single-photon exponential wavepacket (Sec. 2 (b)),
  *   phi(x) = i sqrt(alpha Gamma) exp(i k x + alpha Gamma (x+a)/2) theta(-x-a),
- * or the Gaussian wavepacket (2 pi sigma^2)^(-1/4) exp(i k x -(x-xc)^2/(4 sigma^2))
+ * the plane wave A exp(i k x) theta(-x-a) with A = 1 (Sec. 2 (a)), or the
+ * Gaussian wavepacket (2 pi sigma^2)^(-1/4) exp(i k x -(x-xc)^2/(4 sigma^2))
  * with the same cut theta(-x-a).  theta(0) = 1: the front sits at x = -a. */
 static cplx phi_at(const orc_params* p, double x) {
   double a = half_a(p);
   if (x > -a + 1e-12 * p->delta) return 0.0;
+  if (p->init_cond == 1) return cexp(I * p->k * x); /* plane wave, Sec. 2 (a), A = 1 */
   if (p->init_cond == 4) {
     double s2 = p->sigma * p->sigma;
     double amp = pow(2.0 * M_PI * s2, -0.25) * exp(-(x - p->center) * (x - p->center) / (4.0 * s2));
@@ -284,6 +288,36 @@ static int e0exp_at(const orc_params* p, double t, cplx* out) {
     sum += t1 + t2;
   }
   *out = cexp(-I * p->k * a) * (lead - I * sqrt(ag) * sum);
+  return st;
+}
+
+/* e0(t) of the two-photon plane wave, Sec. 2 (a), with A = 1:
+ *   e0(t) = i sqrt(Gamma/2) e^{-ika} (e^{-ikt} - e^{-Wt}) / p
+ *           - e^{-ika} sum_{n>=1} (Gamma/2)^{n-1/2} / n! [ (t-2na)^n e^{-W(t-2na)}
+ *             + i^n (k-w0) / p^{n+1} gamma(n+1, -ip(t-2na)) e^{-ik(t-2na)} ] theta(t-2na),
+ * p = k - w0 + i Gamma/2 (never 0).  With gamma(n+1,z) = z^{n+1} G(n+1,z),
+ *   i^n / p^{n+1} gamma(n+1, -ipu) = i^n (-i)^{n+1} u^{n+1} G(n+1, -ipu) = -i u^{n+1} G(n+1,-ipu). */
+static int e0plane_at(const orc_params* p, double t, cplx* out) {
+  double a = half_a(p), G2 = 0.5 * p->gamma;
+  cplx W = CMPLX(G2, p->omega0);
+  cplx pp = CMPLX(p->k - p->omega0, G2);
+  int st = ORC_OK;
+  double gr, gi;
+  int br;
+  cplx lead = I * sqrt(G2) * (cexp(-I * p->k * t) - cexp(-W * t)) / pp;
+  cplx sum = 0;
+  for (int n = 1;; ++n) {
+    double u = t - 2.0 * n * a;
+    if (u < 0.0) break;
+    if (u == 0.0) continue; /* both bracket terms vanish at u = 0 */
+    cplx t1 = cexp((n - 0.5) * log(G2) + n * log(u) - lgamma(n + 1.0) - W * u);
+    cplx z = -I * pp * u;
+    if (orc_G(n + 1, creal(z), cimag(z), &gr, &gi, &br) != ORC_OK) st = ORC_NOT_CONVERGED;
+    cplx t2 = -I * (p->k - p->omega0) * CMPLX(gr, gi) *
+              cexp((n - 0.5) * log(G2) + (n + 1) * log(u) - lgamma(n + 1.0) - I * p->k * u);
+    sum += t1 + t2;
+  }
+  *out = cexp(-I * p->k * a) * (lead - sum);
   return st;
 }
 
@@ -405,6 +439,7 @@ int orc_e_at(const orc_params* p, double t, double* re, double* im) {
   cplx v = 0;
   int st = ORC_OK;
   if (t < 0.0) v = 0.0;
+  else if (p->init_cond == 1) st = e0plane_at(p, t, &v);
   else if (p->init_cond == 2) v = e1_at(p, t);
   else if (p->init_cond == 3) st = e0exp_at(p, t, &v);
   else if (p->init_cond == 4) st = e0gauss_at(p, t, &v);
@@ -429,7 +464,8 @@ int orc_etable(const orc_params* p, int64_t n, double* out) {
 /* ------------------------------------------------------------------------ */
 
 /* Prefactor C of psi(x<-a,t) = C phi(x-t) e(t): 1 for stimulated emission
- * (Sec. 2 (b)), sqrt(2) for two identical photons (Sec. 2 (c), last line). */
+ * (Sec. 2 (b)), sqrt(2) for two identical photons (Sec. 2 (c), last line) and
+ * sqrt(2) A with A = 1 for the plane wave (Sec. 2 (a)). */
 static double psi_prefactor(const orc_params* p) { return p->init_cond == 2 ? 1.0 : sqrt(2.0); }
 
 typedef struct {
@@ -457,7 +493,8 @@ static cplx psi_get(orc_state* s, int64_t n_now, int64_t r, int64_t c) {
 static double theta_half(int64_t v) { return v > 0 ? 1.0 : (v == 0 ? 0.5 : 0.0); }
 
 /* chi(x1,x2,0): zero for stimulated emission; phi(x1) phi(x2) for two
- * identical photons (A = 1/sqrt 2 in Sec. 2 (c)). */
+ * identical photons (A = 1/sqrt 2 in Sec. 2 (c)) and for the plane wave
+ * (A^2 e^{ik(x1+x2)} with A = 1, Sec. 2 (a)). */
 static cplx chi0(const orc_params* p, double x1, double x2) {
   if (p->init_cond == 2) return 0.0;
   return phi_at(p, x1) * phi_at(p, x2);
@@ -529,8 +566,8 @@ static int check_params(const orc_params* p) {
   if (p->D < 2 || (p->D & 1)) return ORC_BAD_ARG;
   if (p->nt < 1 || p->nx < 1) return ORC_BAD_ARG;
   if (!(p->delta > 0) || !(p->gamma > 0)) return ORC_BAD_ARG;
-  if (p->init_cond < 2 || p->init_cond > 4) return ORC_BAD_ARG;
-  if (p->init_cond != 4 && !(p->alpha > 0)) return ORC_BAD_ARG;
+  if (p->init_cond < 1 || p->init_cond > 4) return ORC_BAD_ARG;
+  if ((p->init_cond == 2 || p->init_cond == 3) && !(p->alpha > 0)) return ORC_BAD_ARG;
   if (p->init_cond == 4 && !(p->sigma > 0)) return ORC_BAD_ARG;
   return ORC_OK;
 }

@@ -22,6 +22,10 @@ def phi_exp(x, k, alpha, gamma, a):
     return 1j * np.sqrt(ag) * np.exp(1j * k * x + 0.5 * ag * (x + a)) if x <= -a else 0.0
 
 
+def phi_plane(x, k, a):
+    return np.exp(1j * k * x) if x <= -a else 0.0
+
+
 def phi_gauss(x, k, sigma, center, a):
     if x > -a:
         return 0.0

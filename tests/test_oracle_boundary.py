@@ -109,3 +109,26 @@ def test_wavepackets_normalised(oracle):
     A = math.sqrt((4 * (k1 - k2) ** 2 + (a1 + a2) ** 2 * Gm ** 2)
                   / (4 * (k1 - k2) ** 2 + (a1 + a2) ** 2 * Gm ** 2 + 4 * a1 * a2 * Gm ** 2))
     assert abs(A - 1 / math.sqrt(2)) < 1e-15
+
+
+@pytest.mark.parametrize("dk", [0.0, 0.3, -0.8])
+def test_e0_plane_wave_solves_delay_equation(oracle, dk):
+    # Sec. 2 (a): the atom driven by the plane wave e^{ikx} theta(-x-a), e(0) = 0
+    p = params(oracle, init_cond=1, k=PI / 2 + dk)
+    ev = R.solve(p.a, p.gamma, p.omega0, 12.0, phi=lambda x: R.phi_plane(x, p.k, p.a))
+    for t in TIMES:
+        assert abs(oracle.e_at(p, t) - ev(t)) < 1e-11 * max(1.0, abs(ev(t)))
+
+
+@pytest.mark.parametrize("dk,k0a", [(0.0, PI / 2), (0.5, PI / 4), (-0.3, 0.7)])
+def test_e0_plane_wave_steady_state(oracle, dk, k0a):
+    # Driven at e^{-ikt}, the delay equation settles to e(t) = E e^{-ikt} with
+    #   E (W - ik - (Gamma/2) e^{2ika}) = sqrt(Gamma/2) (e^{-ika} - e^{ika})
+    a = 0.5
+    w0 = k0a / a
+    p = params(oracle, init_cond=1, D=20, delta=2 * a / 20, omega0=w0, k=w0 + dk)
+    W = 0.5 * p.gamma + 1j * w0
+    E = math.sqrt(0.5 * p.gamma) * (np.exp(-1j * p.k * a) - np.exp(1j * p.k * a)) \
+        / (W - 1j * p.k - 0.5 * p.gamma * np.exp(2j * p.k * a))
+    t = 150.0  # every transient mode has decayed below 1e-8 by then
+    assert abs(oracle.e_at(p, t) * np.exp(1j * p.k * t) - E) < 1e-8 * abs(E)

@@ -30,7 +30,7 @@ def P(O, D, nrows, nx, ic=3, dk=0.0, alpha=1.0, **kw):
                     alpha=alpha, **kw)
 
 
-@pytest.mark.parametrize("ic,kw", [(2, {}), (3, {}), (3, dict(dk=0.4, alpha=0.7)),
+@pytest.mark.parametrize("ic,kw", [(1, {}), (1, dict(dk=0.3)), (2, {}), (3, {}), (3, dict(dk=0.4, alpha=0.7)),
                                    (4, dict(sigma=0.8, center=-1.0 - 6.4))])
 def test_validation_left_second_order(oracle, ic, kw):
     errs = []
