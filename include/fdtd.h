@@ -135,6 +135,7 @@ enum {
                            /* fdtd_readout_instance).  Snapshots are not included.  */
   FDTD_READ_PROBES = 7,    /* psi at the points of fdtd_set_probes, complex128, in  */
                            /* the order given (0 where the march has not yet been)  */
+  FDTD_READ_CHI = 8,       /* chi at the points of fdtd_set_chi_points, complex128  */
   FDTD_READ_MEASURES = 5   /* App. D, per snapshot row n marched so far: 4 doubles  */
                            /* (Re mu, Im mu, lambda, det M = |mu|^2 lambda); needs   */
                            /* FDTD_IC_STIM_EMISSION, tstep >= 0, FDTD_F64/F64_DW.    */
@@ -231,6 +232,25 @@ fdtd_status fdtd_readout(fdtd_plan_t plan, int32_t kind, void* dst, int64_t dst_
  * FDTD_ERR_UNSUPPORTED (FDTD_F32_COMP plans), FDTD_ERR_CUDA.
  */
 fdtd_status fdtd_set_probes(fdtd_plan_t plan, const int64_t* points, int64_t count);
+
+/*
+ * fdtd_set_chi_points -- the two-photon wavefunction chi(x1, x2, t) by Eq. 2
+ * (the formal solution in terms of psi; Table 1's save_chi writes
+ * chi(a+delta, a+delta+tau, t)) at grid points: pts, host memory, count
+ * triples (i1, i2, n) for x1 = i1 delta, x2 = i2 delta, t = n delta.
+ *   chi = chi(x1-t, x2-t, 0) - (sqrt(Gamma)/2) [ T(x1,x2) + T(x2,x1) ],
+ *   T(y1,y2) = psi(y1-y2-a, t-y2-a) theta(y2+a) theta(t-y2-a)
+ *            - psi(y1-y2+a, t-y2+a) theta(y2-a) theta(t-y2+a),   theta(0) = 1/2;
+ * psi at x <= -a is the exact boundary, psi at marched points is recorded by
+ * probes that this call registers (replacing those of fdtd_set_probes; at most
+ * 4 per point, count <= max_probes / 4).  Call after fdtd_set_boundary and
+ * before the rows the points need are marched; FDTD_READ_CHI evaluates chi
+ * from the recorded values.  FDTD_F64 / FDTD_F64_DW plans.  Errors:
+ * FDTD_ERR_INVALID_ARG (a term right of the box, beyond nt or the wavepacket
+ * table, count too large), FDTD_ERR_STATE (no boundary, or a needed row
+ * already marched), FDTD_ERR_UNSUPPORTED (batched plans), FDTD_ERR_CUDA.
+ */
+fdtd_status fdtd_set_chi_points(fdtd_plan_t plan, const int64_t* pts, int64_t count);
 
 /* Size in bytes that fdtd_readout(kind) writes at the current state. */
 int64_t fdtd_readout_bytes(fdtd_plan_t plan, int32_t kind);

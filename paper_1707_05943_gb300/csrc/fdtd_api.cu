@@ -180,8 +180,8 @@ fdtd_status fdtd_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n_ins
   cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
   int maxg = P->dw ? fdtd::march_dw_max_grid(P->device) : fdtd::march_f64_max_grid(P->device);
   if (maxg <= 0) return FDTD_ERR_CUDA;
-  // one CTA per SM, but at least 64 columns per CTA
-  int grid = P->num_sms < maxg ? P->num_sms : maxg;
+  // one CTA per SM (FDTD_F64_DW: every co-resident CTA), but at least 64 columns per CTA
+  int grid = P->dw ? maxg : (P->num_sms < maxg ? P->num_sms : maxg);
   if ((int64_t)grid > (p.nx + 63) / 64) grid = (int)((p.nx + 63) / 64);
   if (grid > fdtd::kMaxGrid) grid = fdtd::kMaxGrid;
   if (grid < 1) grid = 1;
@@ -237,6 +237,9 @@ fdtd_status fdtd_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n_ins
     P->off_probes = off;
     off = align_up(off + sizeof(int) * (size_t)(p.nt + 1 + 2 * p.max_probes) + 16);
     off = align_up(off + sizeof(cd) * (size_t)p.max_probes);
+    // chi points: up to max_probes / 4 records and their values
+    P->off_chi = off;
+    off = align_up(off + (sizeof(fdtd::ChiRec) + sizeof(cd)) * (size_t)(p.max_probes / 4 + 1));
   }
   if (p.init_cond == FDTD_IC_STIM_EMISSION) {
     P->off_e0tab = off;  off = align_up(off + sizeof(cd) * (size_t)p.nt);
@@ -329,6 +332,11 @@ fdtd_status fdtd_set_boundary(fdtd_plan_t P, int32_t source, const void* device_
     for (int b = 0; b < P->grid; ++b) maxL = (split[b + 1] - split[b] > maxL) ? split[b + 1] - split[b] : maxL;
     size_t need = sizeof(cd) * (size_t)(maxL + P->khalo);
     P->march_smem = (need <= size_t(200) * 1024) ? need : 0;
+    // the double-float march runs every co-resident CTA: the pair sums must not
+    // lower the CTAs that fit on an SM, else they are recomputed from the ring
+    if (P->dw && P->march_smem &&
+        (int64_t)fdtd::march_dw_blocks_per_sm(P->march_smem) * P->num_sms < P->grid)
+      P->march_smem = 0;
   }
   e = cudaMemcpyAsync(P->ws + P->off_colsplit, split, sizeof(int64_t) * (size_t)(P->grid + 1), cudaMemcpyHostToDevice,
                       s);
@@ -380,6 +388,7 @@ fdtd_status fdtd_set_boundary(fdtd_plan_t P, int32_t source, const void* device_
   }
   P->rows_done = 1;
   P->n_probes = 0;
+  P->n_chi = 0;
   if (source == FDTD_BOUNDARY_RESTORE) {
     int64_t done = 1;
     fdtd_status st = state_restore(P, device_table, n, s, &done);
@@ -393,10 +402,82 @@ fdtd_status fdtd_set_boundary(fdtd_plan_t P, int32_t source, const void* device_
   return FDTD_OK;
 }
 
+static fdtd_status set_probes_impl(fdtd_plan_t P, const int64_t* points, int64_t count);
+
 fdtd_status fdtd_set_probes(fdtd_plan_t P, const int64_t* points, int64_t count) {
   if (!P) return FDTD_ERR_INVALID_ARG;
   if (P->batched) return fail(P, FDTD_ERR_UNSUPPORTED, "probes need an FDTD_F64 or FDTD_F64_DW plan");
   if (P->state < 2) return fail(P, FDTD_ERR_STATE, "fdtd_set_probes before fdtd_set_boundary");
+  P->n_chi = 0;
+  return set_probes_impl(P, points, count);
+}
+
+// Eq. 2 at grid points (i1, i2, n): the four psi terms, each a probe of a
+// marched point or the exact value of x <= -a, and the incident chi0.
+fdtd_status fdtd_set_chi_points(fdtd_plan_t P, const int64_t* pts, int64_t count) {
+  if (!P) return FDTD_ERR_INVALID_ARG;
+  if (P->batched) return fail(P, FDTD_ERR_UNSUPPORTED, "chi needs an FDTD_F64 or FDTD_F64_DW plan");
+  if (P->state < 2) return fail(P, FDTD_ERR_STATE, "fdtd_set_chi_points before fdtd_set_boundary");
+  const fdtd_params& p = P->p;
+  if (count < 0 || (count > 0 && !pts) || count > p.max_probes / 4)
+    return fail(P, FDTD_ERR_INVALID_ARG, "chi point count negative or above max_probes / 4");
+  const int64_t Dh = p.D / 2;
+  auto theta = [](int64_t v) { return v > 0 ? 1.0 : (v == 0 ? 0.5 : 0.0); };
+  std::vector<fdtd::ChiRec> recs((size_t)count);
+  std::vector<int64_t> probes;
+  probes.reserve((size_t)(4 * count));
+  for (int64_t q = 0; q < count; ++q) {
+    const int64_t i1 = pts[3 * q], i2 = pts[3 * q + 1], n = pts[3 * q + 2];
+    if (n < 0 || n >= p.nt) return fail(P, FDTD_ERR_INVALID_ARG, "chi point row outside [0, nt)");
+    fdtd::ChiRec& r = recs[q];
+    memset(&r, 0, sizeof r);
+    for (int sw = 0; sw < 2; ++sw) {
+      const int64_t y1 = sw ? i2 : i1, y2 = sw ? i1 : i2;
+      for (int side = 0; side < 2; ++side) {  // psi(y1-y2-+a, t-y2-+a) theta(y2+-a) theta(t-y2-+a)
+        const int t = 2 * sw + side;
+        const int64_t c = side ? y1 - y2 + Dh : y1 - y2 - Dh, row = side ? n - y2 + Dh : n - y2 - Dh;
+        const double w = side ? -theta(y2 - Dh) * theta(row) : theta(y2 + Dh) * theta(row);
+        r.w[t] = w;
+        if (w == 0.0) continue;
+        if (row >= p.nt) return fail(P, FDTD_ERR_INVALID_ARG, "chi point needs a row beyond nt");
+        if (c <= -Dh) {  // x <= -a: C phi((c - row) delta) e(row delta)
+          const int64_t ti = row - c - Dh;
+          if (ti >= P->nphi) return fail(P, FDTD_ERR_INVALID_ARG, "chi point reaches past the wavepacket table");
+          r.kind[t] = 2;
+          r.idx[t] = (int32_t)ti;
+          r.row[t] = (int32_t)row;
+        } else {
+          const int64_t j = c + Dh - 1;
+          if (j >= p.nx) return fail(P, FDTD_ERR_INVALID_ARG, "chi point needs psi right of the marched box");
+          if (row < P->rows_done && row > 0)
+            return fail(P, FDTD_ERR_STATE, "chi point needs a row marched before the call");
+          r.kind[t] = row == 0 ? 0 : 1;  // psi(x > -a, 0) = 0
+          r.idx[t] = (int32_t)(probes.size() / 2);
+          if (row > 0) {
+            probes.push_back(row);
+            probes.push_back(j);
+          }
+        }
+      }
+    }
+    const int64_t f1 = n - i1 - Dh, f2 = n - i2 - Dh;  // phitab index of phi((i - n) delta) if x - t <= -a
+    r.phi1 = (f1 >= 0 && f1 < P->nphi) ? (int32_t)f1 : -1;
+    r.phi2 = (f2 >= 0 && f2 < P->nphi) ? (int32_t)f2 : -1;
+    if ((f1 >= P->nphi) || (f2 >= P->nphi))
+      return fail(P, FDTD_ERR_INVALID_ARG, "chi point reaches past the wavepacket table");
+  }
+  fdtd_status st = set_probes_impl(P, probes.data(), (int64_t)(probes.size() / 2));
+  if (st != FDTD_OK) return st;
+  if (count > 0) {
+    cudaError_t e = cudaMemcpyAsync(P->ws + P->off_chi, recs.data(), sizeof(fdtd::ChiRec) * (size_t)count,
+                                    cudaMemcpyHostToDevice, P->stream);
+    if (e != cudaSuccess) return cuda_fail(P, e, "chi upload");
+  }
+  P->n_chi = count;
+  return FDTD_OK;
+}
+
+static fdtd_status set_probes_impl(fdtd_plan_t P, const int64_t* points, int64_t count) {
   const fdtd_params& p = P->p;
   if (count < 0 || count > p.max_probes || (count > 0 && !points))
     return fail(P, FDTD_ERR_INVALID_ARG, "probe count negative or above max_probes");
@@ -579,6 +660,7 @@ int64_t fdtd_readout_bytes(fdtd_plan_t P, int32_t kind) {
     case FDTD_READ_ROWS_DONE: return (int64_t)sizeof(int64_t);
     case FDTD_READ_STATE: return state_bytes(P, 0);
     case FDTD_READ_PROBES: return (int64_t)sizeof(cd) * P->n_probes;
+    case FDTD_READ_CHI: return (int64_t)sizeof(cd) * P->n_chi;
     case FDTD_READ_MEASURES: {
       if (p.init_cond != FDTD_IC_STIM_EMISSION || !P->nsnap) return -1;
       if (P->rows_done == 0) return 0;
@@ -629,6 +711,15 @@ fdtd_status fdtd_readout(fdtd_plan_t P, int32_t kind, void* dst, int64_t dst_byt
       return st == FDTD_OK ? FDTD_OK : fail(P, st, "checkpoint copy");
     }
     case FDTD_READ_PROBES: src = probe_view(P).val; break;
+    case FDTD_READ_CHI: {
+      const fdtd::ChiRec* recs = at<fdtd::ChiRec>(P, P->off_chi);
+      double2* vals = reinterpret_cast<double2*>(P->ws + P->off_chi + sizeof(fdtd::ChiRec) * (size_t)(p.max_probes / 4 + 1));
+      e = fdtd::launch_chi(recs, P->n_chi, probe_view(P).val, at<cd>(P, P->off_phi), at<cd>(P, P->off_etab), P->C,
+                           p.gamma, p.init_cond != FDTD_IC_STIM_EMISSION, vals, P->stream);
+      if (e != cudaSuccess) return cuda_fail(P, e, "chi kernel");
+      src = vals;
+      break;
+    }
     case FDTD_READ_MEASURES:
       e = fdtd::launch_measures(at<cd>(P, P->off_snaps), p.nx, p.tstep, need / (int64_t)(4 * sizeof(double)),
                                 at<cd>(P, P->off_etab), at<cd>(P, P->off_e0tab), at<cd>(P, P->off_phi),

@@ -48,7 +48,8 @@ constexpr int kF32MaxTrunc = 16;     // |c2|^16 < 2^-26 required (|c2| < 0.32)
 constexpr int kClusterMax = 16;      // CTAs per cluster at most
 
 // double-float march (march_dw.cu)
-constexpr int kDwThreads = 512;      // threads per CTA
+constexpr int kDwThreads = 256;      // threads per CTA; two CTAs per SM
+constexpr int kDwCtasPerSm = 2;
 constexpr int kDwP = 4;              // leading columns of a segment kept in registers
 constexpr int kDwSlack = 32;         // ring rows beyond D+2: how far a CTA may run ahead of its readers
 constexpr int kDwMaxDeps = 4096;     // (cta, lag) entries of the dependency lists, all CTAs together
@@ -224,9 +225,9 @@ struct fdtd_plan_s {
   size_t off_dwtab = 0, off_done = 0, off_deps = 0, off_rowout = 0;
   // stimulated-emission plans: one-excitation e0 table and the App. D measures
   size_t off_e0tab = 0, off_meas = 0;
-  // probes (fdtd_set_probes)
-  size_t off_probes = 0;
-  int64_t n_probes = 0;
+  // probes (fdtd_set_probes) and chi points (fdtd_set_chi_points)
+  size_t off_probes = 0, off_chi = 0;
+  int64_t n_probes = 0, n_chi = 0;
   int64_t rows_per_launch = 0;
   // complex64 (batched) plans
   bool batched = false;
@@ -281,6 +282,17 @@ cudaError_t launch_etable_batch(const EtabArgs* dev_args, int n, int64_t max_nt,
 cudaError_t launch_boundary_post(const BoundaryArgs& a, cudaStream_t s);
 cudaError_t launch_gamma_star(const int32_t* n, const double* z, double* out, int64_t count, cudaStream_t s);
 cudaError_t launch_etable_e0(const BoundaryArgs& a, cd* e0tab, cd* hscratch, cudaStream_t s);
+// one point of the two-photon wavefunction chi (Eq. 2), resolved on the host:
+// chi = chi0 - (sqrt(Gamma)/2) sum_t w[t] psi_t, psi_t a probe value (kind 1) or
+// the exact C phi e of x <= -a (kind 2, phitab[idx] etab[row])
+struct ChiRec {
+  double w[4];
+  int32_t kind[4], idx[4], row[4];
+  int32_t phi1, phi2;  // phitab indices of the incident chi0 = phi(x1-t) phi(x2-t); -1: zero
+  int32_t pad[2];
+};
+cudaError_t launch_chi(const ChiRec* recs, int64_t count, const double2* probe_val, const cd* phitab,
+                       const cd* etab, double C, double gamma, bool incident, double2* out, cudaStream_t s);
 cudaError_t launch_measures(const cd* snaps, int64_t nx, int tstep, int64_t nsnap, const cd* e1tab, const cd* e0tab,
                             const cd* phitab, const double* norms, int D, double delta, double gamma, double alpha,
                             double* out, cudaStream_t s);
@@ -297,6 +309,7 @@ cudaError_t launch_tables_dw(const cd* etab, const cd* phitab, const cd* rowscal
                              int64_t nt, int64_t nphi, int D, float4* etabC, float4* phitab_dw, float4* rowscal_dw,
                              float4* detab_dw, cudaStream_t s);
 cudaError_t launch_march_dw(const DwArgs& a, int grid, size_t smem, cudaStream_t s);
+int march_dw_blocks_per_sm(size_t smem);
 cudaError_t launch_norms_dw(const double* partials, int grid, int64_t n_begin, int64_t n_end, const cd* etab,
                             const cd* phitab, double C, double delta, double* norms, cudaStream_t s);
 cudaError_t launch_row_dw(const float4* src, int64_t nx, double2* dst, cudaStream_t s);

@@ -18,7 +18,8 @@
 // as in FP64.  The boundary tables are FP64 tables split into double-floats
 // once per boundary; the per-CTA norm partials are reduced in FP64.
 //
-// Work layout: one persistent cooperative CTA per SM; CTA b owns the columns
+// Work layout: persistent cooperative CTAs, two per SM (while one waits at a
+// barrier or on a neighbour, the other computes); CTA b owns the columns
 // [colsplit[b], colsplit[b+1]) of every row, each thread a contiguous segment
 // of them, with the recurrence carried across segments and CTAs as in
 // march_f64.cu (a carry's influence dies as |c2|^k; it is carried exactly
@@ -313,7 +314,7 @@ __device__ __forceinline__ bool wait_done(const DwArgs& A, int cta, int64_t row)
   }
 }
 
-__global__ void __launch_bounds__(kDwThreads, 1) k_march_dw(const DwArgs A) {
+__global__ void __launch_bounds__(kDwThreads, kDwCtasPerSm) k_march_dw(const DwArgs A) {
   constexpr int P = kDwP;
   extern __shared__ float4 s_h[];  // pair sums, khalo + CTA range entries
   __shared__ zc s_last[kDwThreads];
@@ -606,6 +607,16 @@ __global__ void k_row_dw(const float4* __restrict__ src, int64_t nx, double2* __
   if (j >= nx) return;
   const float4 v = src[j];
   dst[j] = make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+}
+
+// co-resident CTAs per SM at `smem` bytes of dynamic shared memory
+int march_dw_blocks_per_sm(size_t smem) {
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(k_march_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_march_dw, kDwThreads, smem) != cudaSuccess) return 0;
+  return per;
 }
 
 int march_dw_max_grid(int device) {

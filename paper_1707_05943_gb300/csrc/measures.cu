@@ -1,5 +1,7 @@
-// measures.cu -- the non-Markovian measures of App. D on the snapshot rows of a
-// stimulated-emission march (FDTD_READ_MEASURES):
+// measures.cu -- readouts derived from the march: the two-photon wavefunction
+// chi of Eq. 2 (FDTD_READ_CHI, below), and the non-Markovian measures of
+// App. D on the snapshot rows of a stimulated-emission march
+// (FDTD_READ_MEASURES):
 //   mu(t)     = int phi*(x,t) psi(x,t) dx,
 //   lambda(t) = int |psi(x,t)|^2 dx - |e0(t)|^2,
 //   det M_t   = |mu(t)|^2 lambda(t),
@@ -81,6 +83,38 @@ __global__ void __launch_bounds__(kMeasThreads) k_measures(const cd* __restrict_
   }
 }
 }  // namespace
+
+// chi(x1, x2, t) of Eq. 2 from the probes and the exact boundary, one thread per point
+__global__ void k_chi(const ChiRec* __restrict__ recs, int64_t count, const double2* __restrict__ probe_val,
+                      const cd* __restrict__ phitab, const cd* __restrict__ etab, double C, double gamma,
+                      int incident, double2* __restrict__ out) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  const ChiRec& r = recs[q];
+  cd sum = cd{0.0, 0.0};
+  for (int t = 0; t < 4; ++t) {
+    cd v = cd{0.0, 0.0};
+    if (r.kind[t] == 1) {
+      const double2 p = probe_val[r.idx[t]];
+      v = cd{p.x, p.y};
+    } else if (r.kind[t] == 2) {
+      v = C * (phitab[r.idx[t]] * etab[r.row[t]]);
+    }
+    sum = sum + r.w[t] * v;
+  }
+  cd c0 = cd{0.0, 0.0};
+  if (incident && r.phi1 >= 0 && r.phi2 >= 0) c0 = phitab[r.phi1] * phitab[r.phi2];
+  const cd v = c0 - (0.5 * sqrt(gamma)) * sum;
+  out[q] = make_double2(v.re, v.im);
+}
+
+cudaError_t launch_chi(const ChiRec* recs, int64_t count, const double2* probe_val, const cd* phitab, const cd* etab,
+                       double C, double gamma, bool incident, double2* out, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_chi<<<(unsigned)((count + 127) / 128), 128, 0, s>>>(recs, count, probe_val, phitab, etab, C, gamma,
+                                                        incident ? 1 : 0, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_measures(const cd* snaps, int64_t nx, int tstep, int64_t nsnap, const cd* e1tab, const cd* e0tab,
                             const cd* phitab, const double* norms, int D, double delta, double gamma, double alpha,

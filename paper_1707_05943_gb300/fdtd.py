@@ -26,14 +26,15 @@ OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_
 F64, F32_COMP, F64_DW = 0, 1, 2
 IC_STIM_EMISSION, IC_TWO_PHOTON_EXP, IC_TWO_PHOTON_GAUSS = 2, 3, 4
 BOUNDARY_ANALYTIC, BOUNDARY_TABLE, BOUNDARY_RESTORE = 0, 1, 2
-READ_ROW, READ_NORMS, READ_SNAPSHOTS, READ_ETABLE, READ_ROWS_DONE, READ_MEASURES, READ_STATE, READ_PROBES = range(8)
+READ_ROW, READ_NORMS, READ_SNAPSHOTS, READ_ETABLE, READ_ROWS_DONE, READ_MEASURES, READ_STATE, READ_PROBES, \
+    READ_CHI = range(9)
 
 EXPORTS = ["fdtd_plan", "fdtd_bind_workspace", "fdtd_set_boundary", "fdtd_march", "fdtd_readout",
            "fdtd_readout_bytes", "fdtd_destroy", "fdtd_status_string", "fdtd_last_error", "fdtd_gamma_star",
            "fdtd_march_noalloc", "fdtd_noalloc_max_bytes", "fdtd_readout_instance", "fdtd_readout_instance_bytes",
            "fdtd_mlp_param_count", "fdtd_mlp_workspace_bytes", "fdtd_mlp_sync_bf16", "fdtd_mlp_forward",
            "fdtd_mlp_train_step", "fdtd_gemm_bf16", "fdtd_mlp_status", "fdtd_march_graph", "fdtd_alu_probe",
-           "fdtd_geometric_measure", "fdtd_set_probes"]
+           "fdtd_geometric_measure", "fdtd_set_probes", "fdtd_set_chi_points"]
 
 
 class FdtdParams(ctypes.Structure):
@@ -122,11 +123,12 @@ def lib() -> ctypes.CDLL:
         L.fdtd_alu_probe.argtypes = [i32, vp, ctypes.POINTER(ctypes.c_double)]
         L.fdtd_geometric_measure.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_double)]
         L.fdtd_set_probes.argtypes = [vp, vp, i64]
+        L.fdtd_set_chi_points.argtypes = [vp, vp, i64]
         for f in ("fdtd_plan", "fdtd_bind_workspace", "fdtd_set_boundary", "fdtd_march", "fdtd_readout",
                   "fdtd_gamma_star", "fdtd_march_noalloc", "fdtd_readout_instance", "fdtd_mlp_param_count",
                   "fdtd_mlp_workspace_bytes", "fdtd_mlp_sync_bf16", "fdtd_mlp_forward", "fdtd_mlp_train_step",
                   "fdtd_gemm_bf16", "fdtd_mlp_status", "fdtd_march_graph", "fdtd_alu_probe",
-                  "fdtd_geometric_measure", "fdtd_set_probes"):
+                  "fdtd_geometric_measure", "fdtd_set_probes", "fdtd_set_chi_points"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -171,6 +173,12 @@ def fdtd_set_probes(plan, points):
     """points: (count, 2) int64 array of (row n, column index j)."""
     a = np.ascontiguousarray(points, dtype=np.int64).reshape(-1, 2)
     _check(lib().fdtd_set_probes(plan, a.ctypes.data, a.shape[0]), plan, "fdtd_set_probes")
+
+
+def fdtd_set_chi_points(plan, pts):
+    """pts: (count, 3) int64 array of (i1, i2, n): chi at x1 = i1 delta, x2 = i2 delta, t = n delta."""
+    a = np.ascontiguousarray(pts, dtype=np.int64).reshape(-1, 3)
+    _check(lib().fdtd_set_chi_points(plan, a.ctypes.data, a.shape[0]), plan, "fdtd_set_chi_points")
 
 
 def fdtd_march_graph(plan, n_rows: int):
@@ -351,7 +359,7 @@ class Solver:
         if dtype is None:
             dtype = {READ_NORMS: np.float64, READ_ETABLE: np.complex128, READ_ROWS_DONE: np.int64,
                      READ_MEASURES: np.float64, READ_STATE: np.uint8,
-                     READ_PROBES: np.complex128}.get(kind, self.cdtype)
+                     READ_PROBES: np.complex128, READ_CHI: np.complex128}.get(kind, self.cdtype)
         arr = np.empty(max(nbytes, 0) // np.dtype(dtype).itemsize, dtype=dtype)
         if nbytes > 0:
             fdtd_readout(self.plan, kind, arr.ctypes.data, arr.nbytes)
