@@ -59,7 +59,8 @@ typedef struct {
   int32_t D;         /* 2a/delta (the paper's n_x), even, >= 2                 */
   int32_t init_cond; /* 1: two-photon plane wave, 2: stimulated emission,      */
                      /* 3: two identical exponential photons, 4: two          */
-                     /* identical Gaussian photons                            */
+                     /* identical Gaussian photons, 5: two exponential photons */
+                     /* (k, alpha) and (k2, alpha2), Sec. 2 (c)                */
   double delta;      /* grid step, dx = dt (Sec. 2)                           */
   double gamma;      /* decay rate Gamma                                      */
   double omega0;     /* two-level-system frequency                            */
@@ -67,6 +68,8 @@ typedef struct {
   double alpha;      /* exponential width in units of Gamma (Eq. for phi)     */
   double sigma;      /* Gaussian width                                        */
   double center;     /* Gaussian centre x_c                                   */
+  double k2;         /* init_cond 5: carrier of the second photon            */
+  double alpha2;     /* init_cond 5: width of the second photon              */
 } orc_params;
 
 enum { ORC_OK = 0, ORC_BAD_ARG = 1, ORC_NO_MEM = 2, ORC_NOT_CONVERGED = 3, ORC_BAD_READ = 4 };
@@ -203,6 +206,25 @@ int orc_P(int n, double zr, double zi, double* out_re, double* out_im) {
 /* ------------------------------------------------------------------------ */
 
 static double half_a(const orc_params* p) { return 0.5 * p->D * p->delta; } /* a */
+
+/* init_cond 5: photon i (1 or 2) as an exponential packet of its own (k_i, alpha_i) */
+static orc_params photon(const orc_params* p, int i) {
+  orc_params q = *p;
+  q.init_cond = 3;
+  if (i == 2) {
+    q.k = p->k2;
+    q.alpha = p->alpha2;
+  }
+  return q;
+}
+
+/* Sec. 2 (c): the normalisation of chi(x1,x2,0) = (A/sqrt2)[phi1(x1) phi2(x2) + phi1(x2) phi2(x1)],
+ *   A = sqrt( (4(k1-k2)^2 + (a1+a2)^2 G^2) / (4(k1-k2)^2 + (a1+a2)^2 G^2 + 4 a1 a2 G^2) ). */
+static double pair_norm(const orc_params* p) {
+  double dk = p->k - p->k2, s = p->alpha + p->alpha2, G = p->gamma;
+  double num = 4.0 * dk * dk + s * s * G * G;
+  return sqrt(num / (num + 4.0 * p->alpha * p->alpha2 * G * G));
+}
 
 /* phi(x): Eq. for the single-photon exponential wavepacket (Sec. 2 (b)),
  *   phi(x) = i sqrt(alpha Gamma) exp(i k x + alpha Gamma (x+a)/2) theta(-x-a),
@@ -443,7 +465,10 @@ int orc_e_at(const orc_params* p, double t, double* re, double* im) {
   else if (p->init_cond == 2) v = e1_at(p, t);
   else if (p->init_cond == 3) st = e0exp_at(p, t, &v);
   else if (p->init_cond == 4) st = e0gauss_at(p, t, &v);
-  else return ORC_BAD_ARG;
+  else if (p->init_cond == 5) {  /* e0 of the first photon (the second: orc_e2_at) */
+    orc_params q = photon(p, 1);
+    st = e0exp_at(&q, t, &v);
+  } else return ORC_BAD_ARG;
   *re = creal(v);
   *im = cimag(v);
   return st;
@@ -474,13 +499,39 @@ typedef struct {
   int64_t keep;                   /* stored rows: ring of `keep` rows */
   cplx* store;
   const cplx* etab;               /* e(r delta), r = 0..nt-1 */
+  const cplx* etab2;              /* init_cond 5: e0 of the second photon */
   int bad;
 } orc_state;
 
-/* psi(x<=-a, t) = C phi(x - t) e(t), evaluated pointwise. */
+/* psi(x<=-a, t) = C phi(x - t) e(t), evaluated pointwise; for two different
+ * photons (Sec. 2 (c)) A [phi1(x-t) e0^(2)(t) + phi2(x-t) e0^(1)(t)]. */
+static cplx psi_exact_tab(const orc_params* p, const cplx* et1, const cplx* et2, int64_t r, int64_t c) {
+  const double y = (double)(c - r) * p->delta;
+  if (p->init_cond == 5) {
+    orc_params q1 = photon(p, 1), q2 = photon(p, 2);
+    return pair_norm(p) * (phi_at(&q1, y) * et2[r] + phi_at(&q2, y) * et1[r]);
+  }
+  return psi_prefactor(p) * phi_at(p, y) * et1[r];
+}
 static cplx psi_exact(const orc_state* s, int64_t r, int64_t c) {
-  const orc_params* p = s->p;
-  return psi_prefactor(p) * phi_at(p, (double)(c - r) * p->delta) * s->etab[r];
+  return psi_exact_tab(s->p, s->etab, s->etab2, r, c);
+}
+
+/* e(r delta) tables of a march: e for every class, and for init_cond 5 the
+ * second photon's e0 in *e2 (NULL otherwise).  Caller frees both. */
+static int march_etables(const orc_params* p, int64_t n, cplx** e1, cplx** e2) {
+  *e1 = (cplx*)malloc(sizeof(cplx) * (size_t)n);
+  *e2 = NULL;
+  if (!*e1) return ORC_NO_MEM;
+  int st = orc_etable(p, n, (double*)*e1);
+  if (p->init_cond == 5) {
+    *e2 = (cplx*)malloc(sizeof(cplx) * (size_t)n);
+    if (!*e2) return ORC_NO_MEM;
+    orc_params q = photon(p, 2);
+    int s2 = orc_etable(&q, n, (double*)*e2);
+    if (s2 != ORC_OK) st = s2;
+  }
+  return st;
 }
 
 static cplx psi_get(orc_state* s, int64_t n_now, int64_t r, int64_t c) {
@@ -497,6 +548,11 @@ static double theta_half(int64_t v) { return v > 0 ? 1.0 : (v == 0 ? 0.5 : 0.0);
  * (A^2 e^{ik(x1+x2)} with A = 1, Sec. 2 (a)). */
 static cplx chi0(const orc_params* p, double x1, double x2) {
   if (p->init_cond == 2) return 0.0;
+  if (p->init_cond == 5) { /* (A/sqrt2)[phi1(x1) phi2(x2) + phi1(x2) phi2(x1)], Sec. 2 (c) */
+    orc_params q1 = photon(p, 1), q2 = photon(p, 2);
+    return pair_norm(p) / sqrt(2.0) *
+           (phi_at(&q1, x1) * phi_at(&q2, x2) + phi_at(&q1, x2) * phi_at(&q2, x1));
+  }
   return phi_at(p, x1) * phi_at(p, x2);
 }
 
@@ -566,8 +622,9 @@ static int check_params(const orc_params* p) {
   if (p->D < 2 || (p->D & 1)) return ORC_BAD_ARG;
   if (p->nt < 1 || p->nx < 1) return ORC_BAD_ARG;
   if (!(p->delta > 0) || !(p->gamma > 0)) return ORC_BAD_ARG;
-  if (p->init_cond < 1 || p->init_cond > 4) return ORC_BAD_ARG;
-  if ((p->init_cond == 2 || p->init_cond == 3) && !(p->alpha > 0)) return ORC_BAD_ARG;
+  if (p->init_cond < 1 || p->init_cond > 5) return ORC_BAD_ARG;
+  if ((p->init_cond == 2 || p->init_cond == 3 || p->init_cond == 5) && !(p->alpha > 0)) return ORC_BAD_ARG;
+  if (p->init_cond == 5 && !(p->alpha2 > 0)) return ORC_BAD_ARG;
   if (p->init_cond == 4 && !(p->sigma > 0)) return ORC_BAD_ARG;
   return ORC_OK;
 }
@@ -598,10 +655,12 @@ int orc_march(const orc_params* p, int64_t n_rows, int64_t tstep, double* snaps,
   s.ncols = p->nx;
   s.keep = p->D + 2;
   s.store = (cplx*)calloc((size_t)(s.keep * s.ncols), sizeof(cplx));
-  cplx* et = (cplx*)malloc(sizeof(cplx) * (size_t)n_rows);
-  if (!s.store || !et) { free(s.store); free(et); return ORC_NO_MEM; }
-  st = orc_etable(p, n_rows, (double*)et);
+  cplx *et = NULL, *et2 = NULL;
+  if (!s.store) return ORC_NO_MEM;
+  st = march_etables(p, n_rows, &et, &et2);
+  if (st == ORC_NO_MEM) { free(s.store); free(et); free(et2); return ORC_NO_MEM; }
   s.etab = et;
+  s.etab2 = et2;
   /* Row 0: psi(x, 0) = 0 in x > -a for every class (phi vanishes there). */
   for (int64_t n = 0; n < n_rows; ++n) {
     cplx* row = &s.store[(n % s.keep) * s.ncols];
@@ -618,6 +677,7 @@ int orc_march(const orc_params* p, int64_t n_rows, int64_t tstep, double* snaps,
   int bad = s.bad;
   free(s.store);
   free(et);
+  free(et2);
   if (bad) return ORC_BAD_READ;
   return st;
 }
@@ -641,10 +701,12 @@ int orc_march_left(const orc_params* p, int64_t n_rows, int64_t L, double* grid)
   s.ncols = L;
   s.keep = n_rows; /* full grid */
   s.store = (cplx*)calloc((size_t)(s.keep * s.ncols), sizeof(cplx));
-  cplx* et = (cplx*)malloc(sizeof(cplx) * (size_t)n_rows);
-  if (!s.store || !et) { free(s.store); free(et); return ORC_NO_MEM; }
-  st = orc_etable(p, n_rows, (double*)et);
+  cplx *et = NULL, *et2 = NULL;
+  if (!s.store) return ORC_NO_MEM;
+  st = march_etables(p, n_rows, &et, &et2);
+  if (st == ORC_NO_MEM) { free(s.store); free(et); free(et2); return ORC_NO_MEM; }
   s.etab = et;
+  s.etab2 = et2;
   for (int64_t n = 0; n < n_rows; ++n) {
     cplx* row = &s.store[n * s.ncols];
     for (int64_t m = s.m_first; m <= s.m_last; ++m)
@@ -654,6 +716,7 @@ int orc_march_left(const orc_params* p, int64_t n_rows, int64_t L, double* grid)
   int bad = s.bad;
   free(s.store);
   free(et);
+  free(et2);
   if (bad) return ORC_BAD_READ;
   return st;
 }
@@ -783,18 +846,18 @@ int orc_chi(const orc_params* p, int64_t n_rows, const double* grid, const int64
   if (st != ORC_OK) return st;
   if (n_rows < 1 || n_rows > p->nt) return ORC_BAD_ARG;
   const int64_t Dh = p->D / 2;
-  const double dl = p->delta, C = psi_prefactor(p);
+  const double dl = p->delta;
   const cplx* g = (const cplx*)grid;
-  cplx* et = (cplx*)malloc(sizeof(cplx) * (size_t)n_rows);
-  if (!et) return ORC_NO_MEM;
-  st = orc_etable(p, n_rows, (double*)et);
+  cplx *et = NULL, *et2 = NULL;
+  st = march_etables(p, n_rows, &et, &et2);
+  if (st == ORC_NO_MEM) { free(et); free(et2); return ORC_NO_MEM; }
   int bad = 0;
   /* psi at column c (x = c delta), row r */
   #define ORC_PSI(c, r, dst)                                                        \
     do {                                                                            \
       if ((r) < 0) { dst = 0; break; }                                              \
       if ((r) >= n_rows) { bad = 1; dst = 0; break; }                               \
-      if ((c) <= -Dh) dst = C * phi_at(p, (double)((c) - (r)) * dl) * et[r];        \
+      if ((c) <= -Dh) dst = psi_exact_tab(p, et, et2, (r), (c));                    \
       else if ((c) - (-Dh + 1) >= p->nx) { bad = 1; dst = 0; }                     \
       else dst = g[(r) * p->nx + ((c) - (-Dh + 1))];                                \
     } while (0)
@@ -816,16 +879,36 @@ int orc_chi(const orc_params* p, int64_t n_rows, const double* grid, const int64
   }
   #undef ORC_PSI
   free(et);
+  free(et2);
   if (bad) return ORC_BAD_READ;
   return st;
 }
 
-/* psi(x<=-a, t) on the grid, for the tests: C phi((c-r) delta) e(r delta). */
+/* psi(x<=-a, t) on the grid, for the tests: C phi((c-r) delta) e(r delta)
+ * (two terms for init_cond 5). */
 int orc_psi_exact(const orc_params* p, int64_t r, int64_t c, double* re, double* im) {
   double er, ei;
   int st = orc_e_at(p, r * p->delta, &er, &ei);
-  cplx v = psi_prefactor(p) * phi_at(p, (double)(c - r) * p->delta) * CMPLX(er, ei);
+  cplx e1 = CMPLX(er, ei), e2 = 0;
+  if (p->init_cond == 5) {
+    orc_params q = photon(p, 2);
+    int s2 = orc_e_at(&q, r * p->delta, &er, &ei);
+    if (s2 != ORC_OK) st = s2;
+    e2 = CMPLX(er, ei);
+  }
+  /* single-entry tables indexed at row 0 */
+  cplx v = psi_exact_tab(p, &e1, &e2, 0, c - r);
   *re = creal(v);
   *im = cimag(v);
   return st;
 }
+
+/* e0 of the second photon of init_cond 5 (the first: orc_e_at). */
+int orc_e2_at(const orc_params* p, double t, double* re, double* im) {
+  if (p->init_cond != 5) return ORC_BAD_ARG;
+  orc_params q = photon(p, 2);
+  return orc_e_at(&q, t, re, im);
+}
+
+/* A of Sec. 2 (c) for init_cond 5 (1/sqrt2 for identical photons). */
+double orc_pair_norm(const orc_params* p) { return pair_norm(p); }

@@ -48,6 +48,8 @@ class OrcParams(ctypes.Structure):
         ("alpha", ctypes.c_double),
         ("sigma", ctypes.c_double),
         ("center", ctypes.c_double),
+        ("k2", ctypes.c_double),
+        ("alpha2", ctypes.c_double),
     ]
 
 
@@ -75,8 +77,11 @@ def lib():
         L.orc_measures.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p]
         L.orc_chi.argtypes = [P, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+        L.orc_e2_at.argtypes = [P, ctypes.c_double, dp, dp]
+        L.orc_pair_norm.argtypes = [P]
+        L.orc_pair_norm.restype = ctypes.c_double
         for f in (L.orc_G, L.orc_P, L.orc_phi, L.orc_e_at, L.orc_etable, L.orc_march, L.orc_march_left,
-                  L.orc_psi_exact, L.orc_phi1, L.orc_e0_at, L.orc_measures, L.orc_chi):
+                  L.orc_psi_exact, L.orc_phi1, L.orc_e0_at, L.orc_measures, L.orc_chi, L.orc_e2_at):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -106,10 +111,12 @@ class Params:
     alpha: float = 1.0
     sigma: float = 0.0
     center: float = 0.0
+    k2: float = 0.0
+    alpha2: float = 0.0
 
     def c(self) -> OrcParams:
         return OrcParams(self.nx, self.nt, self.D, self.init_cond, self.delta, self.gamma, self.omega0, self.k,
-                         self.alpha, self.sigma, self.center)
+                         self.alpha, self.sigma, self.center, self.k2, self.alpha2)
 
     @property
     def a(self) -> float:
@@ -232,3 +239,17 @@ def chi(p: Params, grid: np.ndarray, pts) -> np.ndarray:
     _check(lib().orc_chi(ctypes.byref(cp), g.shape[0], g.ctypes.data, q.ctypes.data, q.shape[0], out.ctypes.data),
            "orc_chi")
     return out
+
+
+def e2_at(p: Params, t: float) -> complex:
+    """init_cond 5: e0 of the second photon."""
+    re, im = ctypes.c_double(), ctypes.c_double()
+    cp = p.c()
+    _check(lib().orc_e2_at(ctypes.byref(cp), float(t), ctypes.byref(re), ctypes.byref(im)), "orc_e2_at")
+    return complex(re.value, im.value)
+
+
+def pair_norm(p: Params) -> float:
+    """A of Sec. 2 (c) for two exponential photons (k, alpha), (k2, alpha2)."""
+    cp = p.c()
+    return float(lib().orc_pair_norm(ctypes.byref(cp)))

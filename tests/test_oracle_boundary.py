@@ -16,6 +16,8 @@ PI = math.pi
 
 def params(O, **kw):
     base = dict(nx=64, nt=64, D=40, delta=0.05, gamma=1.0, omega0=PI / 2, k=PI / 2, init_cond=3, alpha=1.0)
+    if kw.get("init_cond") == 5:
+        base.update(k2=PI / 2, alpha2=1.0)
     base.update(kw)
     return O.Params(**base)
 
@@ -132,3 +134,27 @@ def test_e0_plane_wave_steady_state(oracle, dk, k0a):
         / (W - 1j * p.k - 0.5 * p.gamma * np.exp(2j * p.k * a))
     t = 150.0  # every transient mode has decayed below 1e-8 by then
     assert abs(oracle.e_at(p, t) * np.exp(1j * p.k * t) - E) < 1e-8 * abs(E)
+
+
+def test_pair_normalisation_closed_form(oracle):
+    # Sec. 2 (c): A normalises chi(x1,x2,0) = (A/sqrt2)[phi1(x1)phi2(x2) + phi1(x2)phi2(x1)]:
+    # int int |chi|^2 = A^2 (1 + |<phi1|phi2>|^2) = 1, with the overlap integrated here
+    p = params(oracle, init_cond=5, k=PI / 2 + 0.3, alpha=0.7, k2=PI / 2 - 0.5, alpha2=1.4)
+    p1 = params(oracle, init_cond=3, k=p.k, alpha=p.alpha)
+    p2 = params(oracle, init_cond=3, k=p.k2, alpha=p.alpha2)
+    x = np.linspace(-80.0, -p.a, 400001)
+    ov = np.trapezoid(np.conj([oracle.phi(p1, v) for v in x[::4]]) * np.array([oracle.phi(p2, v) for v in x[::4]]),
+                      x[::4])
+    A = oracle.pair_norm(p)
+    assert abs(A * A * (1 + abs(ov) ** 2) - 1.0) < 2e-4
+    # identical photons: A = 1/sqrt2
+    same = params(oracle, init_cond=5, k=p.k, alpha=p.alpha, k2=p.k, alpha2=p.alpha)
+    assert abs(oracle.pair_norm(same) - 1 / math.sqrt(2)) < 1e-15
+
+
+def test_pair_e_tables_are_the_single_photon_ones(oracle):
+    # each photon's e0 is the one-excitation amplitude of that photon alone (Sec. 2 (c))
+    p = params(oracle, init_cond=5, k=PI / 2 + 0.3, alpha=0.7, k2=PI / 2 - 0.5, alpha2=1.4)
+    for t in TIMES:
+        assert oracle.e_at(p, t) == oracle.e_at(params(oracle, init_cond=3, k=p.k, alpha=p.alpha), t)
+        assert oracle.e2_at(p, t) == oracle.e_at(params(oracle, init_cond=3, k=p.k2, alpha=p.alpha2), t)

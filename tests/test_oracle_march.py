@@ -31,7 +31,8 @@ def P(O, D, nrows, nx, ic=3, dk=0.0, alpha=1.0, **kw):
 
 
 @pytest.mark.parametrize("ic,kw", [(1, {}), (1, dict(dk=0.3)), (2, {}), (3, {}), (3, dict(dk=0.4, alpha=0.7)),
-                                   (4, dict(sigma=0.8, center=-1.0 - 6.4))])
+                                   (4, dict(sigma=0.8, center=-1.0 - 6.4)),
+                                   (5, dict(dk=0.3, alpha=0.7, k2=PI / 2 - 0.5, alpha2=1.4))])
 def test_validation_left_second_order(oracle, ic, kw):
     errs = []
     for D in (20, 40, 80):
@@ -133,3 +134,41 @@ def test_app_b_conversions_reproduce_captions():
     for s in sets.values():
         if isinstance(s, dict) and "nx" in s:
             assert s["nx"] % 2 == 0 and s["nx"] <= 2 * s["Nx"]
+
+
+def test_pair_of_equal_photons_is_the_identical_class(oracle):
+    # init_cond 5 with (k2, alpha2) = (k, alpha) is init_cond 3 (A = 1/sqrt2): the marches agree
+    D, nrows = 20, 400
+    same = oracle.march(P(oracle, D, nrows, 200, ic=5, dk=0.2, alpha=0.8, k2=PI / 2 + 0.2, alpha2=0.8), nrows,
+                        tstep=0)["snaps"]
+    ident = oracle.march(P(oracle, D, nrows, 200, ic=3, dk=0.2, alpha=0.8), nrows, tstep=0)["snaps"]
+    assert np.max(np.abs(same - ident)) < 1e-14 * np.abs(ident).max()
+
+
+def test_two_different_photons_probability_conserved(oracle):
+    # int |psi|^2 + int int |chi|^2 = 1 for two different exponential photons (Sec. 2 (c)),
+    # chi by Eq. 2 (orc_chi), psi at x <= -a from the exact boundary; first order in delta
+    dev = []
+    for D in (20, 40, 80):
+        dl = 2.0 / D
+        Dh = D // 2
+        t_end, Ltail = 8.0, 24.0
+        n = int(round(t_end / dl))
+        nx = n + D + 4
+        p = P(oracle, D, n + 1, nx, ic=5, dk=0.3, alpha=0.7, k2=PI / 2 - 0.4, alpha2=1.3)
+        res = oracle.march(p, n + 1, tstep=0)
+        i = np.arange(int(np.floor((-p.a + t_end - Ltail) / dl)), n + Dh + 3)
+        I1, I2 = np.meshgrid(i, i, indexing="ij")
+        pts = np.stack([I1.ravel(), I2.ravel(), np.full(I1.size, n)], axis=1)
+        chi = oracle.chi(p, res["snaps"], pts).reshape(I1.shape)
+        w = np.ones(len(i))
+        w[0] = w[-1] = 0.5
+        p_chi = dl * dl * np.einsum("i,j,ij->", w, w, np.abs(chi) ** 2)
+        cols = np.arange(-Dh - int(Ltail / dl), -Dh + 1)
+        left = np.array([abs(oracle.psi_exact(p, n, c)) ** 2 for c in cols])
+        wl = np.ones(len(cols))
+        wl[0] = wl[-1] = 0.5
+        # trapezoid up to x = -a; with the march's norm (a trapezoid from x = -a) the node at -a has weight 1
+        p_left = dl * np.dot(wl, left)
+        dev.append(abs(p_chi + p_left + res["norms"][n] - 1.0))
+    assert dev[2] < 0.05 and dev[1] / dev[2] > 1.6 and dev[0] / dev[1] > 1.6, dev
