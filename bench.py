@@ -2,17 +2,24 @@
 
 One step = one pass of the whole path on one instance: plan the boundary
 (e(t) kernel, wavepacket and source tables) and march every row of the
-workload.  Default workload: the large FP64 instance, 2^20 marched columns x
-2^18 rows, D = 2000 (2a = 20/Gamma), k0 a = 0.3 pi, Gaussian pulse sigma =
-5/Gamma.  Its ring of D+2 rows is 33.6 GB, far larger than L2, so no L2 flush
-is needed between steps.
+workload.  Default workload: the large instance, 2^20 marched columns x 2^18
+rows, D = 2000 (2a = 20/Gamma), k0 a = 0.3 pi, Gaussian pulse sigma = 5/Gamma,
+marched to FP64 accuracy by the double-float march (FDTD_F64_DW: FP32 pairs,
+held to the same 1e-12 relative L2 against the FP64 oracle as the complex128
+march; --precision f64 times the complex128 march instead).  Its ring of
+D+34 rows x 2^20 x 16 B is 34 GB, far larger than L2, so no L2 flush is needed
+between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 N > 1 runs N independent replicas (one per rank, launched by torchrun); the
 value is the updates of all ranks over the slowest rank's time.  The
 reference arm (--impl reference) times the CPU oracle on a bounded sample of
-the same workload.
+the same workload.  At N = 1 the line also carries "variants": the complex128
+march on a prefix of the same workload, the seeded complex64 batch and the
+complex64 precision instance (each with its error against the FP64 march and
+its march rate over the FP64 march's), and the surrogate network, each timed
+with its own CUDA events and clock record.
 
 Other workloads, one JSON line each:
   --workload small      the 1024 x 4096 FP64 parity instance
@@ -192,8 +199,11 @@ def main():
     ap.add_argument("--D", type=int, default=0, help="use this D at the same delta (profiling)")
     ap.add_argument("--rows-per-launch", type=int, default=4096)
     ap.add_argument("--mid-weight", type=int, default=0, help="column split weight of -a < x <= 3a (0: default)")
-    ap.add_argument("--precision", default="f64", choices=["f64", "dw"],
-                    help="large/small workloads: FP64 march or the double-float march (same parity bar)")
+    ap.add_argument("--precision", default="dw", choices=["f64", "dw"],
+                    help="large/small workloads: the double-float march (default) or the FP64 march; both are "
+                         "held to the same 1e-12 parity with the FP64 oracle")
+    ap.add_argument("--no-variants", action="store_true", help="large workload: skip the variants object")
+    ap.add_argument("--variant-rows", type=int, default=8193, help="rows of the FP64-march variant")
     ap.add_argument("--ref-rows", type=int, default=4096)
     ap.add_argument("--cpu-rows", type=int, default=6144)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -336,8 +346,9 @@ def main():
                       "k0a": w.omega0 * w.a, "sigma": w.sigma,
                       "precision": "complex128" if prec == fdtd.F64 else "complex double-float (4 x FP32)",
                       "rows_per_launch": rpl, "parallelism": f"replicas x{world}",
-                      "l2": "inputs larger than L2 (ring of D+2 rows = "
-                            f"{(w.D + 2) * w.nx * 16 / 1e9:.1f} GB)"},
+                      "l2": "inputs larger than L2 (ring of "
+                            f"{w.D + 2 + (32 if prec != fdtd.F64 else 0)} rows = "
+                            f"{(w.D + 2 + (32 if prec != fdtd.F64 else 0)) * w.nx * 16 / 1e9:.1f} GB)"},
            "roofline": roof, "gpu_launches": launches_per_step * args.steps, "clocks": clocks}
 
     # end to end through the C ABI with host buffers
@@ -368,9 +379,36 @@ def main():
         out["cpu_baseline"] = {"value": u / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                                "sample": f"oracle march of {nx} columns x {args.cpu_rows} rows of {w.name} "
                                          f"({u:.3g} updates, {dt:.1f} s, FP64, 1 thread)"}
+    solver.close()
+    del solver
+    if rank == 0 and world == 1 and not args.no_variants and args.workload == "large":
+        # the other paths on this GPU, each with its own CUDA-event timing and clock record:
+        # the FP64 march, the complex64 compensated march (seeded batch, precision
+        # instance) with its error against the FP64 march, and the surrogate network
+        torch.cuda.empty_cache()
+        var = {}
+        runs = (("f64_march", lambda: f64_variant(args, args.variant_rows, alu_peaks["fp64"])),
+                ("batch_c64", lambda: c64_variant(args, "batch", 1, 2, peaks, src)),
+                ("precision_c64", lambda: c64_variant(args, "precision", 1, 2, peaks, src)),
+                ("surrogate", lambda: surrogate_variant(args, 1, 3, peaks, src)))
+        for name, fn in runs:
+            try:
+                var[name] = fn()
+            except Exception as e:  # reported, not hidden: the line still carries the headline
+                var[name] = {"error": repr(e)[:400]}
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+        head_march = rpl * w.nx / (avg_ms * 1e-3)  # march-only rate of the headline launches
+        f64v = var.get("f64_march", {}).get("value")
+        ratios = {"headline_march_over_f64_march": head_march / f64v if f64v else None}
+        for k in ("batch_c64", "precision_c64"):
+            mv = var.get(k, {}).get("march_only_value")
+            ratios[f"{k}_march_over_f64_march"] = mv / f64v if (mv and f64v) else None
+        var["ratios"] = ratios
+        var["headline_march_only_value"] = head_march
+        out["variants"] = var
     if rank == 0:
         print(json.dumps(out), flush=True)
-    solver.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -379,21 +417,33 @@ def main():
 def run_variant(args):
     """The complex64 compensated march on the seeded batch or the precision
     instance, or the surrogate network's training and inference; one JSON line."""
-    import ctypes
-
-    import numpy as np
     import torch
 
-    from paper_1707_05943_gb300 import build, fdtd as F
+    from paper_1707_05943_gb300 import build
     build.build()
     rank, world, local = env_rank()
     torch.cuda.set_device(local)
     peaks, src = load_peaks()
     if args.workload == "surrogate":
-        return run_surrogate(args, peaks, src)
+        out = surrogate_variant(args, args.steps, args.warmup, peaks, src)
+    else:
+        out = c64_variant(args, args.workload, args.steps, args.warmup, peaks, src)
+    print(json.dumps(out), flush=True)
 
-    ws_list = W.batch(n=args.batch_n) if args.workload == "batch" else [W.PRECISION]
-    name = f"batch1707_n{len(ws_list)}" if args.workload == "batch" else W.PRECISION.name
+
+def c64_variant(args, which, steps, warmup, peaks, src):
+    """One complex64 plan (the seeded batch, or the precision instance): boundary
+    plus CUDA-graph march per step, CUDA events on the plan's stream; error of the
+    largest instances against the FP64 march."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    from paper_1707_05943_gb300 import fdtd as F
+    local = env_rank()[2]
+    ws_list = W.batch(n=args.batch_n) if which == "batch" else [W.PRECISION]
+    name = f"batch1707_n{len(ws_list)}" if which == "batch" else W.PRECISION.name
 
     def cfg(w, prec, tstep=-1, cluster_ctas=0, mid_weight=0):
         return F.Config(nx=w.nx, nt=w.nt, D=w.D, delta=w.delta, gamma=w.gamma, omega0=w.omega0, k=w.k,
@@ -401,7 +451,7 @@ def run_variant(args):
                         precision=prec, rows_per_launch=0, cluster_ctas=cluster_ctas, mid_weight=mid_weight)
 
     knobs, tuned = {}, None
-    if args.workload == "batch" and not args.no_autotune:
+    if which == "batch" and not args.no_autotune:
         from paper_1707_05943_gb300 import autotune as A
         ch = A.tune([cfg(w, F.F32_COMP) for w in ws_list], rows=256)
         knobs = {"cluster_ctas": ch.cluster_ctas, "mid_weight": ch.mid_weight}
@@ -427,14 +477,14 @@ def run_variant(args):
         if record:
             ev.append((e0, e1, e2))
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sampler.start()
     start.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         step(True)
     stop.record(stream)
     torch.cuda.synchronize()
@@ -483,9 +533,10 @@ def run_variant(args):
         f64 = {"value": updates / dt, "unit": UNIT, "how": "same instances, one FP64 plan each, back to back "
                                                            "(wall clock, plan + boundary + march + norms)"}
     F.fdtd_destroy(plan)
+    del buf
     ach = 16 * updates / (t_march * 1e-3) / 1e9
-    out = {"metric": METRIC, "value": updates * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+    out = {"metric": METRIC, "value": updates * steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+           "steps": steps, "warmup": warmup, "ms_per_step": ms / steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "c64-compensated (FP64 boundary and norms)",
            "data": "synthetic",
            "config": {"workload": name, "instances": len(ws_list), "updates_per_step": updates,
@@ -496,7 +547,7 @@ def run_variant(args):
            "roofline": {"kernel": "k_march_f32c", "bound": "hbm", "achieved": ach, "peak": peaks.get("hbm_gbs"),
                         "unit": "GB/s", "frac": ach / peaks.get("hbm_gbs", 6800.0), "traffic": None,
                         "bytes_per_update": 16, "launch_ms": t_march, "peak_source": src},
-           "boundary_ms": t_bnd, "march_ms": t_march,
+           "boundary_ms": t_bnd, "march_ms": t_march, "march_only_value": updates / (t_march * 1e-3),
            "error_vs_fp64": {"instances": pick, "stored_rows_rel_l2_max": max(errs), "norms_rel_max": max(nerrs),
                              "per_instance": [{"i": i, "nx": ws_list[i].nx, "nt": ws_list[i].nt, "D": ws_list[i].D,
                                                "rel_l2": e, "norms_rel": ne}
@@ -507,10 +558,10 @@ def run_variant(args):
            "clocks": clocks}
     if f64:
         out["fp64_same_instances"] = f64
-    print(json.dumps(out), flush=True)
+    return out
 
 
-def run_surrogate(args, peaks, src):
+def surrogate_variant(args, steps, warmup, peaks, src):
     """Training and inference throughput of one surrogate network (4 -> 512 x 4
     GELU -> 8704, BF16 tensor cores) on random inputs of the surrogate's shape."""
     import torch
@@ -522,10 +573,10 @@ def run_surrogate(args, peaks, src):
     t = torch.randn(batch, S.N_OUT, device="cuda")
     y = torch.empty(batch, S.N_OUT, device="cuda")
     st = torch.cuda.ExternalStream(net.sp)
-    for _ in range(args.warmup * 10):
+    for _ in range(warmup * 10):
         net.train_step(x, t, 1e-4)
     torch.cuda.synchronize()
-    n_steps = 200 * args.steps
+    n_steps = 200 * steps
     sampler = ClockSampler(0)
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     sampler.start()
@@ -544,7 +595,7 @@ def run_surrogate(args, peaks, src):
     fl = 2 * batch * sum(S.DIMS[i] * S.DIMS[i + 1] for i in range(1, len(S.DIMS) - 1))
     ach = 3 * fl / (ms_train * 1e-3) / 1e12
     out = {"metric": "surrogate training samples/s (BF16 tensor cores)", "value": batch / (ms_train * 1e-3),
-           "unit": "samples/s", "n_gpus": 1, "steps": n_steps, "warmup": args.warmup * 10,
+           "unit": "samples/s", "n_gpus": 1, "steps": n_steps, "warmup": warmup * 10,
            "ms_per_step": ms_train, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "bf16 (FP32 accumulation, FP32 master weights)", "data": "synthetic",
            "config": {"workload": "surrogate_4x512x4_8704", "batch": batch,
@@ -554,7 +605,59 @@ def run_surrogate(args, peaks, src):
                         "peak": peaks.get("bf16_tflops"), "unit": "TFLOP/s",
                         "frac": ach / peaks.get("bf16_tflops", 1900.0), "traffic": None, "peak_source": src},
            "clocks": clocks}
-    print(json.dumps(out), flush=True)
+    del net
+    return out
+
+
+def f64_variant(args, rows, alu_fp64):
+    """The native FP64 march (FDTD_F64, k_march_f64) on the first `rows` rows of the
+    large workload, in the default launch size: one untimed pass, one timed pass
+    with CUDA events around every launch on the plan's stream."""
+    import torch
+
+    from paper_1707_05943_gb300 import fdtd as F
+    w = W.LARGE.with_(nt=rows)
+    rpl = args.rows_per_launch
+    stream = torch.cuda.Stream()
+    cfg = F.Config(nx=w.nx, nt=w.nt, D=w.D, delta=w.delta, gamma=w.gamma, omega0=w.omega0, k=w.k,
+                   init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center, tstep=-1,
+                   rows_per_launch=rpl, precision=F.F64)
+    s = F.Solver(cfg, stream=stream)
+    ev = []
+
+    def step(record):
+        s.set_boundary()
+        done = 1
+        while done < w.nt:
+            n = min(rpl, w.nt - done)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.march(n)
+            b.record(stream)
+            if record:
+                ev.append((a, b, n))
+            done += n
+
+    step(False)
+    stream.synchronize()
+    sampler = ClockSampler(env_rank()[2])
+    sampler.start()
+    step(True)
+    stream.synchronize()
+    clocks = sampler.stop()
+    ms = sum(a.elapsed_time(b) for a, b, _ in ev)
+    upd = w.nx * sum(n for _, _, n in ev)
+    full = [a.elapsed_time(b) for a, b, n in ev if n == rpl] or [ms]
+    launch_ms = sum(full) / len(full)
+    ach = FLOPS_PER_UPDATE_F64 * rpl * w.nx / (launch_ms * 1e-3) / 1e12
+    s.close()
+    del s
+    return {"value": upd / (ms * 1e-3), "unit": UNIT, "dtype": "f64", "kernel": "k_march_f64",
+            "rows_measured": rows - 1, "march_ms": ms, "launch_ms": launch_ms,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": alu_fp64, "unit": "TFLOP/s",
+                         "frac": ach / alu_fp64, "flops_per_update": FLOPS_PER_UPDATE_F64,
+                         "peak_source": "measured in this run (fdtd_alu_probe, FP64 FMA)"},
+            "how": f"march only, first {rows} rows of {W.LARGE.name}, CUDA events per launch", "clocks": clocks}
 
 
 def solver_grid(s) -> int:

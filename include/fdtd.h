@@ -72,10 +72,16 @@ typedef enum {
 } fdtd_precision;
 
 typedef enum {
+  FDTD_IC_PLANE_WAVE = 1,       /* Sec. 2 (a): two-photon plane wave e^{ik(x1+x2)},  */
+                                /* amplitude A = 1 (not normalisable; alpha unused) */
   FDTD_IC_STIM_EMISSION = 2,    /* Sec. 2 (b): atom excited, one exponential photon  */
   FDTD_IC_TWO_PHOTON_EXP = 3,   /* Sec. 2 (c): two identical exponential photons     */
-  FDTD_IC_TWO_PHOTON_GAUSS = 4  /* two identical Gaussian photons (same structure as  */
+  FDTD_IC_TWO_PHOTON_GAUSS = 4, /* two identical Gaussian photons (same structure as  */
                                 /* Sec. 2 (c); e(t) by quadrature, no closed form)    */
+  FDTD_IC_TWO_PHOTON_PAIR = 5   /* Sec. 2 (c): two exponential photons (k, alpha) and */
+                                /* (k2, alpha2), chi(x1,x2,0) = (A/sqrt2)[phi1(x1)    */
+                                /* phi2(x2) + phi1(x2) phi2(x1)] with the paper's A;  */
+                                /* FDTD_F64 and FDTD_F64_DW plans                     */
 } fdtd_init_cond;
 
 /* Parameters of one instance, in the physical units of the paper's figure
@@ -102,6 +108,8 @@ typedef struct {
                          /* marches a wide instance, 1..8; 0 = by the widest one  */
   int32_t mid_weight;    /* column split: cost of a column of -a < x <= 3a in     */
                          /* bulk columns, 1..4096; 0 = 16                          */
+  double k2;             /* FDTD_IC_TWO_PHOTON_PAIR: carrier of the second photon */
+  double alpha2;         /* FDTD_IC_TWO_PHOTON_PAIR: its width (> 0)             */
   int64_t max_probes;    /* FDTD_F64 / FDTD_F64_DW: capacity of fdtd_set_probes;  */
                          /* 0 = none                                              */
   int64_t spin_cycles;   /* bound of the march's waits on other CTAs, in SM clock */
@@ -125,7 +133,8 @@ enum {
   FDTD_READ_ROW = 0,       /* last marched row: nx complex (precision's type)       */
   FDTD_READ_NORMS = 1,     /* N(n) for n = 0..rows_done-1: FP64                     */
   FDTD_READ_SNAPSHOTS = 2, /* rows 0, tstep+1, 2(tstep+1), ... marched so far       */
-  FDTD_READ_ETABLE = 3,    /* e(r delta), r = 0..nt-1: complex128                   */
+  FDTD_READ_ETABLE = 3,    /* e(r delta), r = 0..nt-1: complex128 (PAIR: the first  */
+                           /* photon's e0)                                          */
   FDTD_READ_ROWS_DONE = 4, /* int64: rows available (row 0 counts)                  */
   FDTD_READ_STATE = 6,     /* checkpoint: the rows the march still reads (the last  */
                            /* min(rows, D+2), in the plan's storage format), the    */

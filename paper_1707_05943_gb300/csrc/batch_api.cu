@@ -69,8 +69,10 @@ fdtd_status validate(const fdtd_params& p) {
   if (p.struct_size != sizeof(fdtd_params)) return FDTD_ERR_INVALID_ARG;
   if (p.D < 2 || (p.D & 1) || p.nx < p.D || p.nt < 1) return FDTD_ERR_INVALID_ARG;
   if (!(p.delta > 0) || !(p.gamma > 0) || !isfinite(p.omega0) || !isfinite(p.k)) return FDTD_ERR_INVALID_ARG;
-  if (p.init_cond < FDTD_IC_STIM_EMISSION || p.init_cond > FDTD_IC_TWO_PHOTON_GAUSS) return FDTD_ERR_INVALID_ARG;
-  if (p.init_cond != FDTD_IC_TWO_PHOTON_GAUSS && !(p.alpha > 0)) return FDTD_ERR_INVALID_ARG;
+  if (p.init_cond == FDTD_IC_TWO_PHOTON_PAIR) return FDTD_ERR_UNSUPPORTED;  // FP64-accurate plans only
+  if (p.init_cond < FDTD_IC_PLANE_WAVE || p.init_cond > FDTD_IC_TWO_PHOTON_GAUSS) return FDTD_ERR_INVALID_ARG;
+  if ((p.init_cond == FDTD_IC_STIM_EMISSION || p.init_cond == FDTD_IC_TWO_PHOTON_EXP) && !(p.alpha > 0))
+    return FDTD_ERR_INVALID_ARG;
   if (p.init_cond == FDTD_IC_TWO_PHOTON_GAUSS && !(p.sigma > 0)) return FDTD_ERR_INVALID_ARG;
   if (p.tstep < -1 || p.rows_per_launch < 0 || p.spin_cycles < 0) return FDTD_ERR_INVALID_ARG;
   if (p.cluster_ctas < 0 || p.cluster_ctas > 8 || p.mid_weight < 0 || p.mid_weight > 4096) return FDTD_ERR_INVALID_ARG;

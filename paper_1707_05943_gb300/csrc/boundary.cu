@@ -84,6 +84,11 @@ __device__ cd phi_left(const BoundaryArgs& A, double x) {
     sincos(A.k * x, &sn, &cs);
     return cd{amp * cs, amp * sn};
   }
+  if (A.init_cond == FDTD_IC_PLANE_WAVE) {  // Sec. 2 (a): e^{ikx}, A = 1
+    double sn, cs;
+    sincos(A.k * x, &sn, &cs);
+    return cd{cs, sn};
+  }
   double ag = A.alpha * A.gamma;
   cd e = cexp_d(cd{0.5 * ag * (x + a), A.k * x});
   double r = sqrt(ag);
@@ -105,14 +110,20 @@ __device__ cd e1_at(const BoundaryArgs& A, double t) {
 }
 
 // h(tau) for the exponential wavepacket: sum_j (Gamma/2)^j g0 u^{j+1} e^{-kappa u} G(j+1,-ipu)/j!.
+// The plane wave of Sec. 2 (a) is the same sum with alpha = 0 and the packet's
+// amplitude i sqrt(alpha Gamma) replaced by 1: g0 = sqrt(Gamma/2) e^{-ika},
+// kappa = ik, p = k - w0 + i Gamma/2.
 __device__ cd h_exp(const BoundaryArgs& A, double tau, unsigned int* status) {
   if (tau <= 0.0) return cd{0.0, 0.0};
+  const bool plane = (A.init_cond == FDTD_IC_PLANE_WAVE);
   const double twoa = A.D * A.delta, a = 0.5 * twoa;
-  const double ag = A.alpha * A.gamma;
+  const double alpha = plane ? 0.0 : A.alpha;
+  const double ag = alpha * A.gamma;
   const double kr = 0.5 * ag, ki = A.k;                            // kappa
-  const cd mip = cd{0.5 * A.gamma * (1.0 - A.alpha), -(A.k - A.omega0)};  // -i p
+  const cd mip = cd{0.5 * A.gamma * (1.0 - alpha), -(A.k - A.omega0)};  // -i p
   const double lg2 = log(0.5 * A.gamma);
-  const double lg0 = 0.5 * log(0.5 * ag * A.gamma);               // |g0| = sqrt(alpha Gamma^2 / 2)
+  // |g0| = sqrt(alpha Gamma^2 / 2) for the packet, sqrt(Gamma / 2) for the plane wave
+  const double lg0 = plane ? 0.5 * log(0.5 * A.gamma) : 0.5 * log(0.5 * ag * A.gamma);
   cd s = cd{0.0, 0.0};
   for (int j = 0;; ++j) {
     double u = tau - j * twoa;
@@ -125,9 +136,9 @@ __device__ cd h_exp(const BoundaryArgs& A, double tau, unsigned int* status) {
     cd G = gstar_scaled(j + 1, u * mip, status);
     s = s + cexp_d(cd{lw, -ki * u}) * G;
   }
-  // g0 = i sqrt(alpha Gamma^2/2) e^{-ika}
+  // g0 = i sqrt(alpha Gamma^2/2) e^{-ika} (packet), sqrt(Gamma/2) e^{-ika} (plane wave)
   cd g0 = cexp_d(cd{lg0, -A.k * a});
-  g0 = cd{-g0.im, g0.re};
+  if (!plane) g0 = cd{-g0.im, g0.re};
   return g0 * s;
 }
 
@@ -201,7 +212,7 @@ __device__ __forceinline__ void etable_row(const EtabArgs& E, int64_t r) {
   double t = r * A.delta;
   if (A.init_cond == FDTD_IC_STIM_EMISSION) {
     A.etab[r] = e1_at(A, t);
-  } else if (A.init_cond == FDTD_IC_TWO_PHOTON_EXP) {
+  } else if (A.init_cond == FDTD_IC_TWO_PHOTON_EXP || A.init_cond == FDTD_IC_PLANE_WAVE) {
     E.h[r] = h_exp(A, t, A.status);
   } else {
     E.h[r] = h_gauss(A, t, E.panels);
@@ -274,8 +285,42 @@ __global__ void k_detab(const BoundaryArgs A) {
 
 // norms[0] = delta * (1/2) |psi(-a, 0)|^2: psi(x>-a, 0) = 0 in every class.
 __global__ void k_norm0(const BoundaryArgs A) {
-  cd v = A.C * (A.phitab[0] * A.etab[0]);
+  cd v = A.phitab[0] * A.etab[0];
+  if (A.phitab2) v = v + A.phitab2[0] * A.etab2[0];  // second term of a photon pair
+  v = A.C * v;
   A.norms[0] = A.delta * 0.5 * cabs2(v);
+}
+
+// Row scalars of a photon pair (Sec. 2 (c)).  psi(x<=-a) = A [phi1(x-t) e0^(2)(t) +
+// phi2(x-t) e0^(1)(t)] is stored as C (phitab etab + phitab2 etab2) with phitab = phi2,
+// etab = e0^(1), phitab2 = phi1, etab2 = e0^(2), C = A.  The mirror bars then give
+// R1(n) dE(i) + R1'(n) dE2(i) with R1 from the phi2 table and R1' from the phi1 table
+// (as k_rowscal), and the chi term of line 4 with chi(x1,x2,0) = (A/sqrt2)[phi1(x1)
+// phi2(x2) + phi1(x2) phi2(x1)] gives R2(n) phi2(r2) + R2'(n) phi1(r2), with
+//   R2(n)  = (1/A_coef) sqrt(Gamma) (A/sqrt2) [phi1(x_c-...) ...] built from phi1,
+//   R2'(n) the same from phi2 (A_coef the update's A, entering as cs = 1/A_coef).
+__global__ void k_rowscal_pair(const BoundaryArgs A, const BoundaryArgs A1, const BoundaryArgs A2) {
+  int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= A.nt) return;
+  const int D = A.D, Dh = D / 2;
+  auto P = [&](const cd* tab) {
+    cd v = tab[n];
+    if (n >= 1) v = v + tab[n - 1];
+    if (n >= D) v = v - tab[n - D];
+    if (n >= D + 1) v = v - tab[n - D - 1];
+    return v;
+  };
+  const double g = -0.25 * A.gamma * A.C;
+  A.rowscal[2 * n] = g * (A.cs * P(A.phitab));
+  A.rowscal2[2 * n] = g * (A.cs * P(A.phitab2));
+  auto diff = [&](const BoundaryArgs& B) {  // phi_B(t1) - phi_B(t2) at the square centre
+    cd f1 = (n >= 1) ? phi_left(B, (-Dh - (double)n + 0.5) * A.delta) : cd{0.0, 0.0};
+    cd f2 = (n >= D + 1) ? phi_left(B, (Dh - (double)n + 0.5) * A.delta) : cd{0.0, 0.0};
+    return f1 - f2;
+  };
+  const double h = sqrt(A.gamma) * A.C * M_SQRT1_2;
+  A.rowscal[2 * n + 1] = h * (A.cs * diff(A1));   // multiplies phitab = phi2
+  A.rowscal2[2 * n + 1] = h * (A.cs * diff(A2));  // multiplies phitab2 = phi1
 }
 
 static bool g_gl_ready[64] = {false};
@@ -382,6 +427,44 @@ cudaError_t launch_etable_e0(const BoundaryArgs& a, cd* e0tab, cd* hscratch, cud
   EtabArgs E = etable_args(b, hscratch);
   k_etable_pass1<<<(unsigned)((a.nt + 63) / 64), 64, 0, s>>>(E);
   k_etable_pass2<<<(unsigned)((a.nt + 127) / 128), 128, 0, s>>>(E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_boundary_pair(const BoundaryArgs& a, cd* hscratch, cd* hscratch2, bool compute_etable,
+                                 cudaStream_t s) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaError_t e = upload_gl(dev);
+  if (e != cudaSuccess) return e;
+  // each photon as an exponential packet of its own
+  BoundaryArgs A1 = a, A2 = a;
+  A1.init_cond = A2.init_cond = FDTD_IC_TWO_PHOTON_EXP;
+  A2.k = a.k2;
+  A2.alpha = a.alpha2;
+  const int T = 128;
+  BoundaryArgs t = A2;  // phitab = phi2
+  t.phitab = a.phitab;
+  k_phitab<<<(unsigned)((a.nphi + T - 1) / T), T, 0, s>>>(t);
+  t = A1;  // phitab2 = phi1
+  t.phitab = a.phitab2;
+  k_phitab<<<(unsigned)((a.nphi + T - 1) / T), T, 0, s>>>(t);
+  k_rowscal_pair<<<(unsigned)((a.nt + T - 1) / T), T, 0, s>>>(a, A1, A2);
+  if (compute_etable) {
+    BoundaryArgs e1 = A1, e2 = A2;  // etab = e0^(1), etab2 = e0^(2)
+    e1.etab = a.etab;
+    e2.etab = a.etab2;
+    EtabArgs E1 = etable_args(e1, hscratch), E2 = etable_args(e2, hscratch2);
+    k_etable_pass1<<<(unsigned)((a.nt + 63) / 64), 64, 0, s>>>(E1);
+    k_etable_pass1<<<(unsigned)((a.nt + 63) / 64), 64, 0, s>>>(E2);
+    k_etable_pass2<<<(unsigned)((a.nt + T - 1) / T), T, 0, s>>>(E1);
+    k_etable_pass2<<<(unsigned)((a.nt + T - 1) / T), T, 0, s>>>(E2);
+  }
+  k_norm0<<<1, 1, 0, s>>>(a);
+  k_detab<<<(unsigned)((a.nt + a.D + T - 1) / T), T, 0, s>>>(a);
+  BoundaryArgs d2 = a;  // detab2 from etab2
+  d2.etab = a.etab2;
+  d2.detab = a.detab2;
+  k_detab<<<(unsigned)((a.nt + a.D + T - 1) / T), T, 0, s>>>(d2);
   return cudaGetLastError();
 }
 

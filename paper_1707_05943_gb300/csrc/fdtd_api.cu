@@ -53,7 +53,7 @@ T* at(fdtd_plan_t p, size_t off) {
   return reinterpret_cast<T*>(p->ws + off);
 }
 
-// Dependency lists of the double-float march (march_dw.cu).  For each CTA b,
+// Dependency lists of the row pipeline (RowDeps in fdtd_internal.cuh).  For each CTA b,
 // every other CTA whose columns b reads, with the smallest lag at which it
 // reads them (row n of b reads row n - lag of that CTA); and, transposed, the
 // CTAs that read b.  The reads of a column j (buffer index) of row n:
@@ -64,11 +64,11 @@ T* at(fdtd_plan_t p, size_t off) {
 //   for D <= j < 2D: 2D-2-j, 2D-1-j at lag j-D+1 (mirror bar of line 3,
 //   row n-m+D/2).
 // Columns outside [0, nx) are x <= -a (exact) and need nothing.
-struct DwDeps {
+struct RowDepLists {
   std::vector<int> dep_off, rd_off, rd;
   std::vector<int2> dep;
 };
-DwDeps build_dw_deps(const int64_t* split, int G, int64_t nx, int D, int khalo) {
+RowDepLists build_row_deps(const int64_t* split, int G, int64_t nx, int D, int khalo) {
   auto owner = [&](int64_t col) {
     int lo = 0, hi = G;  // last b with split[b] <= col
     while (hi - lo > 1) {
@@ -77,8 +77,7 @@ DwDeps build_dw_deps(const int64_t* split, int G, int64_t nx, int D, int khalo) 
     }
     return lo;
   };
-  std::vector<std::vector<int>> lag(G, std::vector<int>());
-  DwDeps d;
+  RowDepLists d;
   d.dep_off.assign(G + 1, 0);
   std::vector<std::vector<int>> readers(G);
   for (int b = 0; b < G; ++b) {
@@ -113,6 +112,29 @@ DwDeps build_dw_deps(const int64_t* split, int G, int64_t nx, int D, int khalo) 
     d.rd_off[b + 1] = (int)d.rd.size();
   }
   return d;
+}
+
+// the second term's tables of a photon pair: e0, phi, R1'/R2', dE2, h scratch, and
+// (double-float plans) the double-float copies of the first four
+struct PairView {
+  cd *etab2, *phitab2, *rowscal2, *detab2, *hscr2;
+  float4* dw;  // C e0, phi, R1'/R2', dE2 (same layout as the first term's)
+};
+PairView pair_view(fdtd_plan_t P) {
+  PairView v;
+  memset(&v, 0, sizeof v);
+  if (!P->off_pair) return v;
+  const fdtd_params& p = P->p;
+  cd* b = reinterpret_cast<cd*>(P->ws + P->off_pair);
+  v.etab2 = b;
+  v.phitab2 = v.etab2 + p.nt;
+  v.rowscal2 = v.phitab2 + P->nphi;
+  v.detab2 = v.rowscal2 + 2 * p.nt;
+  v.hscr2 = v.detab2 + p.nt + p.D;
+  if (P->dw)
+    v.dw = reinterpret_cast<float4*>(
+        P->ws + align_up(P->off_pair + sizeof(cd) * (size_t)(p.nt + P->nphi + 2 * p.nt + p.nt + p.D + p.nt) + 256));
+  return v;
 }
 
 // the probe arrays in the workspace: row offsets, columns, output positions, values
@@ -164,8 +186,11 @@ fdtd_status fdtd_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n_ins
   const fdtd_params& p = *pin;
   if (p.D < 2 || (p.D & 1) || p.nx < p.D || p.nt < 1) return FDTD_ERR_INVALID_ARG;
   if (!(p.delta > 0) || !(p.gamma > 0) || !isfinite(p.omega0) || !isfinite(p.k)) return FDTD_ERR_INVALID_ARG;
-  if (p.init_cond < FDTD_IC_STIM_EMISSION || p.init_cond > FDTD_IC_TWO_PHOTON_GAUSS) return FDTD_ERR_INVALID_ARG;
-  if (p.init_cond != FDTD_IC_TWO_PHOTON_GAUSS && !(p.alpha > 0)) return FDTD_ERR_INVALID_ARG;
+  if (p.init_cond < FDTD_IC_PLANE_WAVE || p.init_cond > FDTD_IC_TWO_PHOTON_PAIR) return FDTD_ERR_INVALID_ARG;
+  if ((p.init_cond == FDTD_IC_STIM_EMISSION || p.init_cond == FDTD_IC_TWO_PHOTON_EXP ||
+       p.init_cond == FDTD_IC_TWO_PHOTON_PAIR) && !(p.alpha > 0))
+    return FDTD_ERR_INVALID_ARG;
+  if (p.init_cond == FDTD_IC_TWO_PHOTON_PAIR && (!(p.alpha2 > 0) || !isfinite(p.k2))) return FDTD_ERR_INVALID_ARG;
   if (p.init_cond == FDTD_IC_TWO_PHOTON_GAUSS && !(p.sigma > 0)) return FDTD_ERR_INVALID_ARG;
   if (p.tstep < -1 || p.rows_per_launch < 0 || p.spin_cycles < 0) return FDTD_ERR_INVALID_ARG;
   if (p.cluster_ctas < 0 || p.cluster_ctas > 8 || p.mid_weight < 0 || p.mid_weight > 4096) return FDTD_ERR_INVALID_ARG;
@@ -197,6 +222,12 @@ fdtd_status fdtd_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n_ins
   P->c3 = (p.gamma / 8.0) * P->cs;
   P->gs = (-p.gamma / 4.0) * P->cs;
   P->C = (p.init_cond == FDTD_IC_STIM_EMISSION) ? 1.0 : sqrt(2.0);
+  if (p.init_cond == FDTD_IC_TWO_PHOTON_PAIR) {
+    // Sec. 2 (c): psi(x<=-a) = A [phi1 e0^(2) + phi2 e0^(1)] with the printed normalisation A
+    const double dk = p.k - p.k2, sa = p.alpha + p.alpha2, G = p.gamma;
+    const double num = 4.0 * dk * dk + sa * sa * G * G;
+    P->C = sqrt(num / (num + 4.0 * p.alpha * p.alpha2 * G * G));
+  }
 
   const double ac2 = cabsh(P->c2);
   // carries are exact while |c2|^k stays above the arithmetic's rounding:
@@ -207,7 +238,7 @@ fdtd_status fdtd_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n_ins
     return FDTD_ERR_UNSUPPORTED;  // |c2| too close to 1 (delta far too coarse)
 
   // workspace layout
-  P->R = p.D + 2 + (P->dw ? fdtd::kDwSlack : 0);
+  P->R = p.D + 2 + fdtd::kRowSlack;
   P->rows_per_launch = p.rows_per_launch > 0 ? p.rows_per_launch : 4096;
   P->elem = sizeof(cd);
   // row pitch: a multiple of 32 columns plus 32, so that ring rows are never a
@@ -223,15 +254,21 @@ fdtd_status fdtd_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n_ins
   P->off_detab = off;    off = align_up(off + sizeof(cd) * (size_t)(p.nt + p.D));
   P->off_norms = off;    off = align_up(off + sizeof(double) * (size_t)p.nt);
   P->off_hscr = off;     off = align_up(off + sizeof(cd) * (size_t)p.nt);
-  const size_t npart = P->dw ? (size_t)P->rows_per_launch * (size_t)grid : 2 * (size_t)grid;
-  P->off_partials = off; off = align_up(off + sizeof(double) * npart);
+  P->off_partials = off; off = align_up(off + sizeof(double) * (size_t)P->rows_per_launch * (size_t)grid);
   P->off_colsplit = off; off = align_up(off + sizeof(int64_t) * (size_t)(grid + 1));
+  P->off_done = off;     off = align_up(off + sizeof(unsigned long long) * (size_t)grid);
+  P->off_deps = off;     off = align_up(off + sizeof(int) * (size_t)(2 * (grid + 1) + 3 * fdtd::kMaxDeps));
   if (P->dw) {
     // double-float tables: C e (nt), phi (nphi), R1/R2 (2 nt), dE (nt + D)
     P->off_dwtab = off;  off = align_up(off + sizeof(float4) * (size_t)(4 * p.nt + P->nphi + p.D));
-    P->off_done = off;   off = align_up(off + sizeof(unsigned long long) * (size_t)grid);
-    P->off_deps = off;   off = align_up(off + sizeof(int) * (size_t)(2 * (grid + 1) + 3 * fdtd::kDwMaxDeps));
     P->off_rowout = off; off = align_up(off + sizeof(cd) * (size_t)p.nx);
+  }
+  if (p.init_cond == FDTD_IC_TWO_PHOTON_PAIR) {
+    // second term: e0 (nt), phi (nphi), R1'/R2' (2 nt), dE2 (nt + D), h scratch (nt);
+    // double-float copies of the first four
+    P->off_pair = off;
+    off = align_up(off + sizeof(cd) * (size_t)(p.nt + P->nphi + 2 * p.nt + p.nt + p.D + p.nt) + 256);
+    if (P->dw) off = align_up(off + sizeof(float4) * (size_t)(4 * p.nt + P->nphi + p.D));
   }
   if (p.max_probes > 0) {  // row offsets (nt + 1), columns, output positions, values
     P->off_probes = off;
@@ -291,6 +328,8 @@ fdtd_status fdtd_set_boundary(fdtd_plan_t P, int32_t source, const void* device_
     return fail(P, FDTD_ERR_INVALID_ARG, "unknown boundary source");
   if (source == FDTD_BOUNDARY_TABLE && (!device_table || n != p.nt))
     return fail(P, FDTD_ERR_INVALID_ARG, "boundary table must hold nt complex128 values");
+  if (source == FDTD_BOUNDARY_TABLE && p.init_cond == FDTD_IC_TWO_PHOTON_PAIR)
+    return fail(P, FDTD_ERR_UNSUPPORTED, "a photon pair's boundary is computed, not given as a table");
   if (source == FDTD_BOUNDARY_RESTORE && (!device_table || n <= 0))
     return fail(P, FDTD_ERR_INVALID_ARG, "checkpoint missing");
   cudaStream_t s = P->stream;
@@ -343,6 +382,7 @@ fdtd_status fdtd_set_boundary(fdtd_plan_t P, int32_t source, const void* device_
   if (e != cudaSuccess) return cuda_fail(P, e, "cudaMemcpyAsync(colsplit)");
   // a copy from pageable memory is staged before cudaMemcpyAsync returns
   fdtd::BoundaryArgs a;
+  memset(&a, 0, sizeof a);
   a.etab = at<cd>(P, P->off_etab);
   a.phitab = at<cd>(P, P->off_phi);
   a.rowscal = at<cd>(P, P->off_rowscal);
@@ -362,7 +402,17 @@ fdtd_status fdtd_set_boundary(fdtd_plan_t P, int32_t source, const void* device_
   a.cs = P->cs;
   a.status = &at<fdtd::SyncWords>(P, P->off_sync)->status;
   a.norms = at<double>(P, P->off_norms);
-  e = fdtd::launch_boundary(a, at<cd>(P, P->off_hscr), source != FDTD_BOUNDARY_TABLE, s);
+  const PairView pv = pair_view(P);
+  a.etab2 = pv.etab2;
+  a.phitab2 = pv.phitab2;
+  a.rowscal2 = pv.rowscal2;
+  a.detab2 = pv.detab2;
+  a.k2 = p.k2;
+  a.alpha2 = p.alpha2;
+  if (p.init_cond == FDTD_IC_TWO_PHOTON_PAIR)
+    e = fdtd::launch_boundary_pair(a, at<cd>(P, P->off_hscr), pv.hscr2, source != FDTD_BOUNDARY_TABLE, s);
+  else
+    e = fdtd::launch_boundary(a, at<cd>(P, P->off_hscr), source != FDTD_BOUNDARY_TABLE, s);
   if (e == cudaSuccess && p.init_cond == FDTD_IC_STIM_EMISSION)  // e0 of the measures (App. D)
     e = fdtd::launch_etable_e0(a, at<cd>(P, P->off_e0tab), at<cd>(P, P->off_hscr), s);
   if (e != cudaSuccess) return cuda_fail(P, e, "boundary kernels");
@@ -370,19 +420,25 @@ fdtd_status fdtd_set_boundary(fdtd_plan_t P, int32_t source, const void* device_
     float4* t = at<float4>(P, P->off_dwtab);
     e = fdtd::launch_tables_dw(a.etab, a.phitab, a.rowscal, a.detab, P->C, p.nt, P->nphi, p.D, t, t + p.nt,
                                t + p.nt + P->nphi, t + 3 * p.nt + P->nphi, s);
-    if (e == cudaSuccess)
-      e = cudaMemsetAsync(P->ws + P->off_done, 0, sizeof(unsigned long long) * (size_t)P->grid, s);
+    if (e == cudaSuccess && pv.dw)
+      e = fdtd::launch_tables_dw(pv.etab2, pv.phitab2, pv.rowscal2, pv.detab2, P->C, p.nt, P->nphi, p.D, pv.dw,
+                                 pv.dw + p.nt, pv.dw + p.nt + P->nphi, pv.dw + 3 * p.nt + P->nphi, s);
     if (e != cudaSuccess) return cuda_fail(P, e, "double-float tables");
-    DwDeps dd = build_dw_deps(split, P->grid, p.nx, p.D, P->khalo);
-    if ((int)dd.dep.size() > fdtd::kDwMaxDeps || (int)dd.rd.size() > fdtd::kDwMaxDeps)
-      return fail(P, FDTD_ERR_UNSUPPORTED, "too many CTA dependencies for the double-float march");
+  }
+  {
+    // the row pipeline: row counters and the CTAs' dependency lists
+    e = cudaMemsetAsync(P->ws + P->off_done, 0, sizeof(unsigned long long) * (size_t)P->grid, s);
+    if (e != cudaSuccess) return cuda_fail(P, e, "cudaMemsetAsync(row counters)");
+    RowDepLists dd = build_row_deps(split, P->grid, p.nx, p.D, P->khalo);
+    if ((int)dd.dep.size() > fdtd::kMaxDeps || (int)dd.rd.size() > fdtd::kMaxDeps)
+      return fail(P, FDTD_ERR_UNSUPPORTED, "too many CTA dependencies for the row pipeline");
     // layout: dep_off[G+1] | rd_off[G+1] | dep (int2) | rd (int)
-    std::vector<int> buf(2 * (P->grid + 1) + 3 * fdtd::kDwMaxDeps, 0);
+    std::vector<int> buf(2 * (P->grid + 1) + 3 * fdtd::kMaxDeps, 0);
     memcpy(buf.data(), dd.dep_off.data(), sizeof(int) * (P->grid + 1));
     memcpy(buf.data() + P->grid + 1, dd.rd_off.data(), sizeof(int) * (P->grid + 1));
     if (!dd.dep.empty()) memcpy(buf.data() + 2 * (P->grid + 1), dd.dep.data(), sizeof(int2) * dd.dep.size());
     if (!dd.rd.empty())
-      memcpy(buf.data() + 2 * (P->grid + 1) + 2 * fdtd::kDwMaxDeps, dd.rd.data(), sizeof(int) * dd.rd.size());
+      memcpy(buf.data() + 2 * (P->grid + 1) + 2 * fdtd::kMaxDeps, dd.rd.data(), sizeof(int) * dd.rd.size());
     e = cudaMemcpyAsync(P->ws + P->off_deps, buf.data(), sizeof(int) * buf.size(), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(P, e, "cudaMemcpyAsync(deps)");
   }
@@ -518,6 +574,17 @@ fdtd_status fdtd_march_graph(fdtd_plan_t P, int64_t n_rows) {
 
 // the double-float march of rows [rows_done, end): one persistent launch per
 // rows_per_launch rows, each followed by the FP64 norm reduction of its rows
+static fdtd::RowDeps row_deps(fdtd_plan_t P) {
+  int* deps = at<int>(P, P->off_deps);
+  fdtd::RowDeps d;
+  d.dep_off = deps;
+  d.rd_off = deps + P->grid + 1;
+  d.dep = reinterpret_cast<const int2*>(deps + 2 * (P->grid + 1));
+  d.rd = deps + 2 * (P->grid + 1) + 2 * fdtd::kMaxDeps;
+  d.done = at<unsigned long long>(P, P->off_done);
+  return d;
+}
+
 static fdtd_status march_dw(fdtd_plan_t P, int64_t end) {
   const fdtd_params& p = P->p;
   fdtd::DwArgs a;
@@ -530,15 +597,17 @@ static fdtd_status march_dw(fdtd_plan_t P, int64_t end) {
   a.phitab = t + p.nt;
   a.rowscal = t + p.nt + P->nphi;
   a.detab = t + 3 * p.nt + P->nphi;
+  const PairView pv = pair_view(P);
+  if (pv.dw) {
+    a.etabC2 = pv.dw;
+    a.phitab2 = pv.dw + p.nt;
+    a.rowscal2 = pv.dw + p.nt + P->nphi;
+    a.detab2 = pv.dw + 3 * p.nt + P->nphi;
+  }
   a.partials = at<double>(P, P->off_partials);
   a.snaps = P->nsnap ? at<double2>(P, P->off_snaps) : nullptr;
   a.colsplit = at<int64_t>(P, P->off_colsplit);
-  int* deps = at<int>(P, P->off_deps);
-  a.dep_off = deps;
-  a.rd_off = deps + P->grid + 1;
-  a.dep = reinterpret_cast<const int2*>(deps + 2 * (P->grid + 1));
-  a.rd = deps + 2 * (P->grid + 1) + 2 * fdtd::kDwMaxDeps;
-  a.done = at<unsigned long long>(P, P->off_done);
+  a.deps = row_deps(P);
   a.sync = at<fdtd::SyncWords>(P, P->off_sync);
   a.nx = p.nx;
   a.nt = p.nt;
@@ -576,8 +645,9 @@ static fdtd_status march_dw(fdtd_plan_t P, int64_t end) {
     a.n_end = (n0 + per < end) ? n0 + per : end;
     cudaError_t e = fdtd::launch_march_dw(a, P->grid, P->march_smem, P->stream);
     if (e == cudaSuccess)
-      e = fdtd::launch_norms_dw(a.partials, P->grid, a.n_begin, a.n_end, at<cd>(P, P->off_etab),
-                                at<cd>(P, P->off_phi), P->C, p.delta, at<double>(P, P->off_norms), P->stream);
+      e = fdtd::launch_norms_rows(a.partials, P->grid, a.n_begin, a.n_end, at<cd>(P, P->off_etab),
+                                  at<cd>(P, P->off_phi), pv.etab2, pv.phitab2, P->C, p.delta,
+                                  at<double>(P, P->off_norms), P->stream);
     if (e != cudaSuccess) return cuda_fail(P, e, "double-float march launch");
   }
   P->rows_done = end;
@@ -603,10 +673,18 @@ fdtd_status fdtd_march(fdtd_plan_t P, int64_t n_rows) {
   a.phitab = at<cd>(P, P->off_phi);
   a.rowscal = at<cd>(P, P->off_rowscal);
   a.detab = at<cd>(P, P->off_detab);
+  {
+    const PairView pv = pair_view(P);
+    a.etab2 = pv.etab2;
+    a.phitab2 = pv.phitab2;
+    a.rowscal2 = pv.rowscal2;
+    a.detab2 = pv.detab2;
+  }
   a.norms = at<double>(P, P->off_norms);
   a.partials = at<double>(P, P->off_partials);
   a.snaps = P->nsnap ? at<cd>(P, P->off_snaps) : nullptr;
   a.colsplit = at<int64_t>(P, P->off_colsplit);
+  a.deps = row_deps(P);
   a.sync = at<fdtd::SyncWords>(P, P->off_sync);
   a.nx = p.nx;
   a.nt = p.nt;
@@ -633,11 +711,14 @@ fdtd_status fdtd_march(fdtd_plan_t P, int64_t n_rows) {
     a.probe_idx = v.idx;
     a.probe_val = v.val;
   }
-  const int64_t per = p.rows_per_launch > 0 ? p.rows_per_launch : 4096;
+  const int64_t per = P->rows_per_launch;
   for (int64_t n0 = P->rows_done; n0 < end; n0 += per) {
     a.n_begin = n0;
     a.n_end = (n0 + per < end) ? n0 + per : end;
     cudaError_t e = fdtd::launch_march_f64(a, P->grid, P->march_smem, P->stream);
+    if (e == cudaSuccess)
+      e = fdtd::launch_norms_rows(a.partials, P->grid, a.n_begin, a.n_end, a.etab, a.phitab, a.etab2, a.phitab2,
+                                  P->C, p.delta, a.norms, P->stream);
     if (e != cudaSuccess) return cuda_fail(P, e, "march launch");
   }
   P->rows_done = end;
@@ -714,8 +795,10 @@ fdtd_status fdtd_readout(fdtd_plan_t P, int32_t kind, void* dst, int64_t dst_byt
     case FDTD_READ_CHI: {
       const fdtd::ChiRec* recs = at<fdtd::ChiRec>(P, P->off_chi);
       double2* vals = reinterpret_cast<double2*>(P->ws + P->off_chi + sizeof(fdtd::ChiRec) * (size_t)(p.max_probes / 4 + 1));
-      e = fdtd::launch_chi(recs, P->n_chi, probe_view(P).val, at<cd>(P, P->off_phi), at<cd>(P, P->off_etab), P->C,
-                           p.gamma, p.init_cond != FDTD_IC_STIM_EMISSION, vals, P->stream);
+      const PairView pv = pair_view(P);
+      e = fdtd::launch_chi(recs, P->n_chi, probe_view(P).val, at<cd>(P, P->off_phi), at<cd>(P, P->off_etab),
+                           pv.phitab2, pv.etab2, P->C, p.gamma, p.init_cond != FDTD_IC_STIM_EMISSION, vals,
+                           P->stream);
       if (e != cudaSuccess) return cuda_fail(P, e, "chi kernel");
       src = vals;
       break;

@@ -51,8 +51,9 @@ constexpr int kClusterMax = 16;      // CTAs per cluster at most
 constexpr int kDwThreads = 256;      // threads per CTA; two CTAs per SM
 constexpr int kDwCtasPerSm = 2;
 constexpr int kDwP = 4;              // leading columns of a segment kept in registers
-constexpr int kDwSlack = 32;         // ring rows beyond D+2: how far a CTA may run ahead of its readers
-constexpr int kDwMaxDeps = 4096;     // (cta, lag) entries of the dependency lists, all CTAs together
+// row pipeline of the FP64 and double-float marches
+constexpr int kRowSlack = 32;        // ring rows beyond D+2: how far a CTA may run ahead of its readers
+constexpr int kMaxDeps = 4096;       // (cta, lag) entries of the dependency lists, all CTAs together
 
 // sync words at the start of the workspace
 struct SyncWords {
@@ -63,19 +64,86 @@ struct SyncWords {
   long long where;         // row at which a device error was latched
 };
 
+// ---------------------------------------------------------------- row pipeline
+// The persistent marches separate rows without a grid barrier: CTA b publishes
+// done[b] = rows it has completed (a release store after its row's stores);
+// before row n it waits (acquire loads, bounded) until each CTA it reads has
+// completed row n - lag (dep: the smallest lag at which b reads that CTA), and
+// until each CTA that reads b has completed row n - 1 - slack (the ring holds
+// D + 2 + slack rows, so the slot of row n is free).  Every wait is for a
+// strictly earlier row, so no set of waits can close a cycle.
+struct RowDeps {
+  const int* dep_off;        // grid+1: CTA b's dependencies are dep[dep_off[b] .. dep_off[b+1])
+  const int2* dep;           // (cta, lag)
+  const int* rd_off;         // grid+1: CTA b's readers are rd[rd_off[b] .. rd_off[b+1])
+  const int* rd;
+  unsigned long long* done;  // per CTA: rows completed (absolute row index + 1)
+};
+
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];\n" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;\n" ::"l"(p), "l"(v) : "memory");
+}
+// wait until done[cta] > row (rows before n_begin are complete: earlier launches
+// finished); false on timeout or when another CTA has latched an error
+__device__ __forceinline__ bool wait_row_done(const RowDeps& P, SyncWords* sync, long long spin_cycles,
+                                              int64_t n_begin, int cta, int64_t row) {
+  if (row < n_begin) return true;
+  const unsigned long long need = (unsigned long long)(row + 1);
+  if (ld_acquire_u64(&P.done[cta]) >= need) return true;
+  const long long t0 = clock64();
+  int k = 0;
+  for (;;) {
+    __nanosleep(64);
+    if (ld_acquire_u64(&P.done[cta]) >= need) return true;
+    if ((++k & 15) == 0 && *(volatile unsigned int*)&sync->status != 0u) return false;
+    if (clock64() - t0 > spin_cycles) return false;
+  }
+}
+// warp 0 of CTA `cta` before row n: returns false (to every lane) if a wait gave up,
+// after latching FDTD_ERR_TIMEOUT; the caller's CTA barrier then publishes the result
+__device__ __forceinline__ bool row_wait_warp(const RowDeps& P, SyncWords* sync, long long spin_cycles,
+                                              int64_t n_begin, int cta, int64_t n, int slack) {
+  const int lane = threadIdx.x & 31;
+  bool ok = true;
+  for (int k = P.dep_off[cta] + lane; k < P.dep_off[cta + 1]; k += 32) {
+    const int2 d = P.dep[k];
+    if (!wait_row_done(P, sync, spin_cycles, n_begin, d.x, n - d.y)) ok = false;
+  }
+  for (int k = P.rd_off[cta] + lane; k < P.rd_off[cta + 1]; k += 32)
+    if (!wait_row_done(P, sync, spin_cycles, n_begin, P.rd[k], n - 1 - slack)) ok = false;
+  ok = __all_sync(0xffffffffu, ok);
+  __threadfence();  // the rows waited for are visible to every thread after the caller's barrier
+  if (!ok && lane == 0 && atomicCAS(&sync->status, 0u, (unsigned)FDTD_ERR_TIMEOUT) == 0u) sync->where = n;
+  return ok;
+}
+#endif
+
 // ---------------------------------------------------------------- march args
 struct MarchArgs {
   cd* ring;              // R rows x stride
   int64_t stride;        // columns per ring row (>= nx)
-  int R;                 // ring rows = D + 2
+  int R;                 // ring rows = D + 2 + kRowSlack
   const cd* etab;        // e(r delta), r < nt
   const cd* phitab;      // phi(-a - j delta), j < nphi
   const cd* rowscal;     // per row: R1(n), R2(n)  (2 per row)
   const cd* detab;       // E(i-D) - E(i), i < nt + D
+  // two different photons (FDTD_IC_TWO_PHOTON_PAIR): psi(x<=-a) = C (phi e + phi2 e2),
+  // the bulk sources gain R1'(n) dE2 + R2'(n) phi2; null otherwise
+  const cd* phitab2;
+  const cd* etab2;
+  const cd* rowscal2;
+  const cd* detab2;
   double* norms;         // nt
-  double* partials;      // 2 x grid
+  double* partials;      // (n - n_begin) * grid + cta: the CTA's trapezoid sum of |psi|^2 on row n
   cd* snaps;             // nsnap x nx or null
   const int64_t* colsplit;  // grid+1 column starts
+  RowDeps deps;          // row pipeline
   SyncWords* sync;
   int64_t n_begin, n_end;   // rows marched by this launch
   int64_t nx, nt, nphi;
@@ -90,7 +158,7 @@ struct MarchArgs {
   int hreuse;            // 1: delay pair sums of the previous row kept in shared memory
   int mid_weight;        // cost of a column of -a < x <= 3a in bulk columns
   cd c2pow[kMaxTrunc + 1];  // c2^0 .. c2^kMaxTrunc
-  long long spin_cycles; // bounded wait of the grid barrier
+  long long spin_cycles; // bound of every wait on another CTA
   // probes: points of row n are probe_col[probe_off[n] .. probe_off[n+1]) (null: none);
   // the value of column probe_col[k] goes to probe_val[probe_idx[k]]
   const int* probe_off;
@@ -103,21 +171,21 @@ struct MarchArgs {
 // A complex value in double-float: (rh + rl) + i (ih + il), stored as float4
 // (rh, ih, rl, il); |rl| <= ulp(rh)/2 once normalised.
 struct DwArgs {
-  float4* ring;          // R rows x stride, R = D + 2 + kDwSlack
+  float4* ring;          // R rows x stride, R = D + 2 + kRowSlack
   int64_t stride;
   int R;
   const float4* etabC;   // C e(r delta), r < nt
   const float4* phitab;  // phi(-a - j delta), j < nphi
   const float4* rowscal; // R1(n), R2(n)
   const float4* detab;   // E(i-D) - E(i), i < nt + D
+  const float4* etabC2;  // second term of a photon pair (as in MarchArgs), null otherwise
+  const float4* phitab2;
+  const float4* rowscal2;
+  const float4* detab2;
   double* partials;      // (n - n_begin) * grid + cta: sum over the CTA's columns of w_j |psi|^2
   double2* snaps;        // complex128 snapshots or null
   const int64_t* colsplit;
-  const int* dep_off;    // grid+1: CTA b's dependencies are dep[dep_off[b] .. dep_off[b+1])
-  const int2* dep;       // (cta, lag): row n of this CTA needs row n - lag of `cta` complete
-  const int* rd_off;     // grid+1: CTA b's readers are rd[rd_off[b] .. rd_off[b+1])
-  const int* rd;
-  unsigned long long* done;  // per CTA: rows completed (absolute row index + 1)
+  RowDeps deps;          // row pipeline
   SyncWords* sync;
   int64_t n_begin, n_end;
   int64_t nx, nt, nphi;
@@ -137,6 +205,12 @@ struct BoundaryArgs {
   cd* phitab;
   cd* rowscal;
   cd* detab;             // nt + D entries, see k_detab
+  // FDTD_IC_TWO_PHOTON_PAIR: the second term's tables (null otherwise) and photon
+  cd* etab2;
+  cd* phitab2;
+  cd* rowscal2;
+  cd* detab2;
+  double k2, alpha2;
   double* norms;         // norms[0] is set here (row 0 is the initial condition)
   int64_t nt, nphi;
   int D;
@@ -225,6 +299,8 @@ struct fdtd_plan_s {
   size_t off_dwtab = 0, off_done = 0, off_deps = 0, off_rowout = 0;
   // stimulated-emission plans: one-excitation e0 table and the App. D measures
   size_t off_e0tab = 0, off_meas = 0;
+  // photon pairs (FDTD_IC_TWO_PHOTON_PAIR): the second term's tables (0: none)
+  size_t off_pair = 0;
   // probes (fdtd_set_probes) and chi points (fdtd_set_chi_points)
   size_t off_probes = 0, off_chi = 0;
   int64_t n_probes = 0, n_chi = 0;
@@ -270,6 +346,9 @@ fdtd_status batch_readout(fdtd_plan_s* P, int32_t inst, int32_t kind, void* dst,
 namespace fdtd {
 // launchers (return cudaError_t)
 cudaError_t launch_boundary(const BoundaryArgs& a, cd* hscratch, bool compute_etable, cudaStream_t s);
+// the boundary of a photon pair (FDTD_IC_TWO_PHOTON_PAIR): both terms' tables
+cudaError_t launch_boundary_pair(const BoundaryArgs& a, cd* hscratch, cd* hscratch2, bool compute_etable,
+                                 cudaStream_t s);
 // the same work in three steps, so that a batch computes every e-table in one launch
 struct EtabArgs {
   BoundaryArgs b;
@@ -292,7 +371,8 @@ struct ChiRec {
   int32_t pad[2];
 };
 cudaError_t launch_chi(const ChiRec* recs, int64_t count, const double2* probe_val, const cd* phitab,
-                       const cd* etab, double C, double gamma, bool incident, double2* out, cudaStream_t s);
+                       const cd* etab, const cd* phitab2, const cd* etab2, double C, double gamma, bool incident,
+                       double2* out, cudaStream_t s);
 cudaError_t launch_measures(const cd* snaps, int64_t nx, int tstep, int64_t nsnap, const cd* e1tab, const cd* e0tab,
                             const cd* phitab, const double* norms, int D, double delta, double gamma, double alpha,
                             double* out, cudaStream_t s);
@@ -310,7 +390,8 @@ cudaError_t launch_tables_dw(const cd* etab, const cd* phitab, const cd* rowscal
                              float4* detab_dw, cudaStream_t s);
 cudaError_t launch_march_dw(const DwArgs& a, int grid, size_t smem, cudaStream_t s);
 int march_dw_blocks_per_sm(size_t smem);
-cudaError_t launch_norms_dw(const double* partials, int grid, int64_t n_begin, int64_t n_end, const cd* etab,
-                            const cd* phitab, double C, double delta, double* norms, cudaStream_t s);
+cudaError_t launch_norms_rows(const double* partials, int grid, int64_t n_begin, int64_t n_end, const cd* etab,
+                             const cd* phitab, const cd* etab2, const cd* phitab2, double C, double delta,
+                             double* norms, cudaStream_t s);
 cudaError_t launch_row_dw(const float4* src, int64_t nx, double2* dst, cudaStream_t s);
 }  // namespace fdtd

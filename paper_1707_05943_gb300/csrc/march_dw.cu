@@ -32,8 +32,8 @@
 // rows it has completed (a release store); before row n it waits (acquire
 // loads, bounded) until every CTA it reads has completed the rows it needs,
 // and until every CTA that reads it has gone far enough that the ring slot of
-// row n is free: the ring holds D + 2 + kDwSlack rows, so a CTA may run up to
-// kDwSlack rows ahead of its readers.  Every wait is for a strictly earlier
+// row n is free: the ring holds D + 2 + kRowSlack rows, so a CTA may run up to
+// kRowSlack rows ahead of its readers (RowDeps in fdtd_internal.cuh).  Every wait is for a strictly earlier
 // row, so the order of rows is a well-founded order and no set of waits can
 // close a cycle; co-residency of all CTAs (cooperative launch) does the rest.
 // CTAs therefore run skewed, each a fraction of a row behind the CTA on its
@@ -166,28 +166,29 @@ __device__ __forceinline__ zc cnorm(const zc& a) {
   return r;
 }
 // |y|^2 added to a real double-float accumulator (h, l), unnormalised
-__device__ __forceinline__ void nacc_add(float& h, float& l, const zc& y, float w) {
+__device__ __forceinline__ void nacc_add(float& h, float& l, const zc& y) {
   float p, e, s, t;
   p = __fmul_rn(y.rh, y.rh);
   e = __fmaf_rn(y.rh, y.rh, -p);
-  e = __fmaf_rn(2.f * y.rh, y.rl, e);
+  e = __fmaf_rn(y.rh + y.rh, y.rl, e);
   float q = __fmul_rn(y.ih, y.ih);
   float f = __fmaf_rn(y.ih, y.ih, -q);
-  f = __fmaf_rn(2.f * y.ih, y.il, f);
-  // w is 1 or 1/2 (trapezoid end), exact
-  two_sum(h, w * p, s, t);
+  f = __fmaf_rn(y.ih + y.ih, y.il, f);
+  two_sum(h, p, s, t);
   h = s;
-  l = __fadd_rn(l, __fadd_rn(t, w * e));
-  two_sum(h, w * q, s, t);
+  l = __fadd_rn(l, __fadd_rn(t, e));
+  two_sum(h, q, s, t);
   h = s;
-  l = __fadd_rn(l, __fadd_rn(t, w * f));
+  l = __fadd_rn(l, __fadd_rn(t, f));
 }
 
 // ---------------------------------------------------------------- reads
 // psi at x = c delta <= -a, t = r delta: phi((c-r) delta) C e(r delta)
 __device__ __forceinline__ zc psi_left_dw(const DwArgs& A, int64_t r, int64_t c) {
   const int Dh = A.D >> 1;
-  return cnorm(cmul(ldz_ro(&A.phitab[r - c - Dh]), ldz_ro(&A.etabC[r])));
+  zc v = cmul(ldz_ro(&A.phitab[r - c - Dh]), ldz_ro(&A.etabC[r]));
+  if (A.phitab2) cmac(v, ldz_ro(&A.phitab2[r - c - Dh]), ldz_ro(&A.etabC2[r]));  // second photon of a pair
+  return cnorm(v);
 }
 
 // psi at an earlier point the update of row n reads; nslot = n % R
@@ -218,6 +219,7 @@ __device__ __noinline__ zc rhs_general_dw(const DwArgs& A, int64_t n, int nslot,
     const zc br = cadd(psi_any_dw(A, n, nslot, r2, -m), psi_any_dw(A, n, nslot, r2, -m + 1));
     cmac(S, zc_of(A.gs), cscale(w, csub(bl, br)));
     cmac(S, R2, ldz_ro(&A.phitab[r2]));  // line 4: phi((m-n) delta) = phitab[r2]
+    if (A.phitab2) cmac(S, ldz_ro(&A.rowscal2[2 * n + 1]), ldz_ro(&A.phitab2[r2]));
   }
   if (m >= Dh + 1) {  // line 3, theta(x - a)
     const int64_t r3 = n - m + Dh;
@@ -240,6 +242,7 @@ struct RowDw {
   float4* row0;
   double2* snap;
   zc R1, R2;
+  zc R1b, R2b;  // second term of a photon pair
   float4* hs;
   int64_t hbase;
   bool cold;
@@ -266,6 +269,10 @@ __device__ __forceinline__ zc rhs_bulk_dw(const DwArgs& A, const RowDw& R, int64
   if (i >= 0) {
     cmac(S, R.R1, ldz_ro(&A.detab[i]));
     if (i >= D) cmac(S, R.R2, ldz_ro(&A.phitab[i - D]));
+    if (A.detab2) {
+      cmac(S, R.R1b, ldz_ro(&A.detab2[i]));
+      if (i >= D) cmac(S, R.R2b, ldz_ro(&A.phitab2[i - D]));
+    }
   }
   return cadd(a, S);
 }
@@ -285,33 +292,7 @@ __device__ __forceinline__ void finalize_dw(const DwArgs& A, const RowDw& R, int
                                             float& nl) {
   stz(R.row0 + j, y);
   if (R.snap) R.snap[j] = make_double2((double)y.rh + (double)y.rl, (double)y.ih + (double)y.il);
-  nacc_add(nh, nl, y, (j == A.nx - 1) ? 0.5f : 1.0f);  // trapezoid end weight at the last column
-}
-
-// ---------------------------------------------------------------- flags
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];\n" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;\n" ::"l"(p), "l"(v) : "memory");
-}
-
-// wait until done[cta] > row (row < n_begin is complete: earlier launches finished).
-// Returns false on timeout or when another CTA has latched an error.
-__device__ __forceinline__ bool wait_done(const DwArgs& A, int cta, int64_t row) {
-  if (row < A.n_begin) return true;
-  const unsigned long long need = (unsigned long long)(row + 1);
-  if (ld_acquire(&A.done[cta]) >= need) return true;
-  const long long t0 = clock64();
-  int k = 0;
-  for (;;) {
-    __nanosleep(64);
-    if (ld_acquire(&A.done[cta]) >= need) return true;
-    if ((++k & 15) == 0 && *(volatile unsigned int*)&A.sync->status != 0u) return false;
-    if (clock64() - t0 > A.spin_cycles) return false;
-  }
+  nacc_add(nh, nl, y);  // the last column's half weight is taken off once per row
 }
 
 __global__ void __launch_bounds__(kDwThreads, kDwCtasPerSm) k_march_dw(const DwArgs A) {
@@ -346,44 +327,44 @@ __global__ void __launch_bounds__(kDwThreads, kDwCtasPerSm) k_march_dw(const DwA
   }
   const int64_t h0 = (j_lo - A.khalo > 0) ? j_lo - A.khalo : 0;
   const int nh = (int)(j_lo - h0);
-  const int dlo = A.dep_off[cta], dhi = A.dep_off[cta + 1];
-  const int rlo = A.rd_off[cta], rhi = A.rd_off[cta + 1];
   s_len[tid] = (int)(s1 - s0);
   if (tid == 0) s_ok = (*(volatile unsigned int*)&A.sync->status == 0u) ? 1 : 0;
   __syncthreads();
   if (!s_ok) return;
 
-  for (int64_t n = A.n_begin; n < A.n_end; ++n) {
+  int slot = (int)(A.n_begin % A.R);  // ring slot of row n
+  int64_t snap_ctr = -1, snap_idx = 0;  // row n is a snapshot row when snap_ctr == 0
+  if (A.snaps && A.tstep >= 0) {
+    snap_ctr = A.n_begin % (A.tstep + 1);
+    snap_idx = A.n_begin / (A.tstep + 1) + (snap_ctr ? 1 : 0);
+  }
+  for (int64_t n = A.n_begin; n < A.n_end; ++n,
+               slot = (slot + 1 == A.R) ? 0 : slot + 1,
+               snap_idx += (snap_ctr == 0) ? 1 : 0,
+               snap_ctr = (snap_ctr < 0) ? -1 : (snap_ctr == A.tstep ? 0 : snap_ctr + 1)) {
     // wait: the rows this CTA reads are complete, and its readers are past the
     // rows that the slot of row n still holds for them (warp 0, one flag per lane)
     if (tid < 32) {
-      bool ok = true;
-      for (int k = dlo + tid; k < dhi; k += 32) {
-        const int2 d = A.dep[k];
-        if (!wait_done(A, d.x, n - d.y)) ok = false;
-      }
-      for (int k = rlo + tid; k < rhi; k += 32)
-        if (!wait_done(A, A.rd[k], n - 1 - kDwSlack)) ok = false;
-      ok = __all_sync(0xffffffffu, ok);
-      __threadfence();  // the rows waited for are visible to every thread after the barrier below
-      if (tid == 0) {
-        if (!ok && atomicCAS(&A.sync->status, 0u, (unsigned)FDTD_ERR_TIMEOUT) == 0u) A.sync->where = n;
-        s_ok = ok ? 1 : 0;
-      }
+      const bool ok = row_wait_warp(A.deps, A.sync, A.spin_cycles, A.n_begin, cta, n, kRowSlack);
+      if (tid == 0) s_ok = ok ? 1 : 0;
     }
     __syncthreads();
     if (!s_ok) return;
 
     RowDw R;
     R.n = n;
-    R.nslot = (int)(n % A.R);
-    R.row1 = A.ring + ((n - 1) % A.R) * A.stride;
-    R.rowD = (n >= D) ? A.ring + ((n - D) % A.R) * A.stride : nullptr;
-    R.rowD1 = (n >= D + 1) ? A.ring + ((n - D - 1) % A.R) * A.stride : nullptr;
-    R.row0 = A.ring + (n % A.R) * A.stride;
-    R.snap = (A.snaps && A.tstep >= 0 && n % (A.tstep + 1) == 0) ? A.snaps + (n / (A.tstep + 1)) * A.nx : nullptr;
+    // ring slots and the snapshot row from running counters (no 64-bit division per row)
+    auto back = [&](int k) { const int t = slot - k; return t < 0 ? t + A.R : t; };
+    R.nslot = slot;
+    R.row1 = A.ring + (int64_t)back(1) * A.stride;
+    R.rowD = (n >= D) ? A.ring + (int64_t)back(D) * A.stride : nullptr;
+    R.rowD1 = (n >= D + 1) ? A.ring + (int64_t)back(D + 1) * A.stride : nullptr;
+    R.row0 = A.ring + (int64_t)slot * A.stride;
+    R.snap = (snap_ctr == 0) ? A.snaps + snap_idx * A.nx : nullptr;
     R.R1 = ldz_ro(&A.rowscal[2 * n]);
     R.R2 = ldz_ro(&A.rowscal[2 * n + 1]);
+    R.R1b = A.rowscal2 ? ldz_ro(&A.rowscal2[2 * n]) : zc0();
+    R.R2b = A.rowscal2 ? ldz_ro(&A.rowscal2[2 * n + 1]) : zc0();
     R.hs = A.hreuse ? s_h : nullptr;
     R.hbase = h0;
     R.cold = (n == A.n_begin);
@@ -408,44 +389,53 @@ __global__ void __launch_bounds__(kDwThreads, kDwCtasPerSm) k_march_dw(const DwA
     float nh_ = 0.f, nl_ = 0.f;
     zc y0[P];
     zc y = zc0();
-    if (s0 >= 2 * (int64_t)D && s0 < s1) {
+    if (s0 >= 2 * (int64_t)D && s0 < s1 && !A.detab2) {
       // a segment of x > 3a only: each column's loads are issued one column ahead,
       // and the stencil and delay neighbours are carried from the column before
-      const float4* r1 = R.row1;
-      const float4* rD = R.rowD;
-      const float4* rD1 = R.rowD1;
+      // per-thread bases; column s0 + k is offset k (32-bit) from each
+      const bool dd = R.rowD != nullptr, dd1 = R.rowD1 != nullptr;
       const bool use_hs = R.hs && !R.cold;
-      zc a = ldz(r1 + s0 - 1);
-      zc pDp = rD ? ldz(rD + s0 - D - 1) : zc0();
-      zc pD1p = (rD1 && !use_hs) ? ldz(rD1 + s0 - D - 1) : zc0();
+      const float4* b1 = R.row1 + s0;                     // row n-1 at column s0
+      const float4* bD = dd ? R.rowD + (s0 - D) : b1;     // row n-D at column s0 - D
+      const float4* bD1 = dd1 ? R.rowD1 + (s0 - D) : b1;  // row n-D-1 at column s0 - D
+      float4* bh = R.hs ? R.hs + (s0 - R.hbase) : nullptr;
       const int64_t i0 = R.n - s0 - 1 + D;  // detab index of column s0 (r2 + D); one less per column
-      zc b_n = ldz(r1 + s0);
-      zc pD_n = rD ? ldz(rD + s0 - D) : zc0();
-      zc pD1_n = (rD1 && !use_hs) ? ldz(rD1 + s0 - D) : zc0();
-      zc hp_n = use_hs ? zc_of(R.hs[s0 - R.hbase]) : zc0();
-      zc E_n = (i0 >= 0) ? ldz_ro(&A.detab[i0]) : zc0();
-      zc F_n = (i0 >= D) ? ldz_ro(&A.phitab[i0 - D]) : zc0();
-      auto col = [&](int64_t j) -> zc {  // r_j from the values loaded for j; loads for j + 1
+      // sources of column s0 + k: detab[i0 - k] while k <= kE, phitab[i0 - D - k] while k <= kF
+      const int kE = (int)(i0 < 0 ? -1 : (i0 < (int64_t)(s1 - s0) ? i0 : s1 - s0));
+      const int kF = (int)(i0 - D < 0 ? -1 : (i0 - D < (int64_t)(s1 - s0) ? i0 - D : s1 - s0));
+      const float4* bE = A.detab + (i0 >= 0 ? i0 : 0);
+      const float4* bF = A.phitab + (i0 - D >= 0 ? i0 - D : 0);
+      const int len = (int)(s1 - s0);
+      zc a = ldz(b1 - 1);
+      zc pDp = dd ? ldz(bD - 1) : zc0();
+      zc pD1p = (dd1 && !use_hs) ? ldz(bD1 - 1) : zc0();
+      zc b_n = ldz(b1);
+      zc pD_n = dd ? ldz(bD) : zc0();
+      zc pD1_n = (dd1 && !use_hs) ? ldz(bD1) : zc0();
+      zc hp_n = use_hs ? zc_of(bh[0]) : zc0();
+      zc E_n = (kE >= 0) ? ldz_ro(bE) : zc0();
+      zc F_n = (kF >= 0) ? ldz_ro(bF) : zc0();
+      auto col = [&](int k) -> zc {  // r of column s0 + k from the values loaded for it; loads for k + 1
         const zc b = b_n, pD = pD_n, pD1 = pD1_n, hpv = hp_n, E = E_n, Fv = F_n;
-        const int64_t i = R.n - j - 1 + D;
-        if (j + 1 < s1) {
-          b_n = ldz(r1 + j + 1);
-          if (rD) pD_n = ldz(rD + j + 1 - D);
-          if (rD1 && !use_hs) pD1_n = ldz(rD1 + j + 1 - D);
-          if (use_hs) hp_n = zc_of(R.hs[j + 1 - R.hbase]);
-          E_n = (i - 1 >= 0) ? ldz_ro(&A.detab[i - 1]) : zc0();
-          F_n = (i - 1 >= D) ? ldz_ro(&A.phitab[i - 1 - D]) : zc0();
+        const int k1 = k + 1;
+        if (k1 < len) {
+          b_n = ldz(b1 + k1);
+          if (dd) pD_n = ldz(bD + k1);
+          if (dd1 && !use_hs) pD1_n = ldz(bD1 + k1);
+          if (use_hs) hp_n = zc_of(bh[k1]);
+          E_n = (k1 <= kE) ? ldz_ro(bE - k1) : zc0();
+          F_n = (k1 <= kF) ? ldz_ro(bF - k1) : zc0();
         }
         zc S = cmul(zc_of(A.d1), a);
         cmac(S, zc_of(A.c2), b);
-        if (rD) {
+        if (dd) {
           const zc hn = cadd(pDp, pD);  // row n-D pair
-          if (rD1) cmac(S, zc_of(A.c3), cadd(hn, use_hs ? hpv : cadd(pD1p, pD1)));
-          if (R.hs) R.hs[j - R.hbase] = make_float4(hn.rh, hn.ih, hn.rl, hn.il);
+          if (dd1) cmac(S, zc_of(A.c3), cadd(hn, use_hs ? hpv : cadd(pD1p, pD1)));
+          if (bh) bh[k] = make_float4(hn.rh, hn.ih, hn.rl, hn.il);
         }
-        if (i >= 0) {
+        if (k <= kE) {
           cmac(S, R.R1, E);
-          if (i >= D) cmac(S, R.R2, Fv);
+          if (k <= kF) cmac(S, R.R2, Fv);
         }
         const zc r = cadd(a, S);
         a = b;
@@ -455,14 +445,14 @@ __global__ void __launch_bounds__(kDwThreads, kDwCtasPerSm) k_march_dw(const DwA
       };
 #pragma unroll
       for (int v = 0; v < P; ++v) {
-        const int64_t j = s0 + v;
-        if (j < s1) y = step_dw(A, col(j), y);
+        if (v < len) y = step_dw(A, col(v), y);
         y0[v] = y;
       }
-      for (int64_t j = s0 + P; j < s1; ++j) {
-        y = step_dw(A, col(j), y);
-        if (j - s0 < A.kfix) stz(R.row0 + j, y);  // provisional: receives the carry in pass B
-        else finalize_dw(A, R, j, y, nh_, nl_);
+      float4* o = R.row0 + s0;
+      for (int k = P; k < len; ++k) {
+        y = step_dw(A, col(k), y);
+        if (k < A.kfix) stz(o + k, y);  // provisional: receives the carry in pass B
+        else finalize_dw(A, R, s0 + k, y, nh_, nl_);
       }
     } else {
 #pragma unroll
@@ -555,30 +545,38 @@ __global__ void __launch_bounds__(kDwThreads, kDwCtasPerSm) k_march_dw(const DwA
       if (tid == 0) s_tot = (double)h + (double)l;
     }
     if (tid == 0) {
-      const double tot = s_tot;
+      double tot = s_tot;
+      if (j_hi == A.nx && j_lo < j_hi) {  // trapezoid end weight: half of the last column
+        const float4 v = R.row0[A.nx - 1];
+        const double re = (double)v.x + (double)v.z, im = (double)v.y + (double)v.w;
+        tot -= 0.5 * (re * re + im * im);
+      }
       A.partials[(n - A.n_begin) * gridDim.x + cta] = tot;
       if (!A.probe_off) {
         __threadfence();
-        st_release(&A.done[cta], (unsigned long long)(n + 1));
+        st_release_u64(&A.deps.done[cta], (unsigned long long)(n + 1));
       }
     }
     if (A.probe_off) {  // the probe values are written before the row is published
       __syncthreads();
       if (tid == 0) {
         __threadfence();
-        st_release(&A.done[cta], (unsigned long long)(n + 1));
+        st_release_u64(&A.deps.done[cta], (unsigned long long)(n + 1));
       }
     }
   }
 }
 
 // N(n) = delta [ (1/2)|psi(-a, n delta)|^2 + sum over CTAs of the partials ], FP64, fixed order
-__global__ void k_norms_dw(const double* __restrict__ partials, int grid, int64_t n_begin, int64_t n_end,
-                           const cd* __restrict__ etab, const cd* __restrict__ phitab, double C, double delta,
-                           double* __restrict__ norms) {
+__global__ void k_norms_rows(const double* __restrict__ partials, int grid, int64_t n_begin, int64_t n_end,
+                             const cd* __restrict__ etab, const cd* __restrict__ phitab,
+                             const cd* __restrict__ etab2, const cd* __restrict__ phitab2, double C, double delta,
+                             double* __restrict__ norms) {
   const int64_t n = n_begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (n >= n_end) return;
-  const cd v = C * (phitab[n] * etab[n]);  // psi(-a, n delta): phi(-a - n delta + n delta)... phitab[n - (-D/2) - D/2]
+  cd v = phitab[n] * etab[n];  // psi(-a, n delta) = C phi(-a - n delta) e(n delta): phitab[n]
+  if (phitab2) v = v + phitab2[n] * etab2[n];
+  v = C * v;
   double t = 0.5 * cabs2(v);
   const double* p = partials + (n - n_begin) * grid;
   for (int b = 0; b < grid; ++b) t += p[b];
@@ -644,12 +642,13 @@ cudaError_t launch_march_dw(const DwArgs& a, int grid, size_t smem, cudaStream_t
   return cudaLaunchCooperativeKernel((const void*)k_march_dw, dim3(grid), dim3(kDwThreads), args, smem, s);
 }
 
-cudaError_t launch_norms_dw(const double* partials, int grid, int64_t n_begin, int64_t n_end, const cd* etab,
-                            const cd* phitab, double C, double delta, double* norms, cudaStream_t s) {
+cudaError_t launch_norms_rows(const double* partials, int grid, int64_t n_begin, int64_t n_end, const cd* etab,
+                             const cd* phitab, const cd* etab2, const cd* phitab2, double C, double delta,
+                             double* norms, cudaStream_t s) {
   const int64_t rows = n_end - n_begin;
   if (rows <= 0) return cudaSuccess;
-  k_norms_dw<<<(unsigned)((rows + 127) / 128), 128, 0, s>>>(partials, grid, n_begin, n_end, etab, phitab, C, delta,
-                                                            norms);
+  k_norms_rows<<<(unsigned)((rows + 127) / 128), 128, 0, s>>>(partials, grid, n_begin, n_end, etab, phitab, etab2,
+                                                              phitab2, C, delta, norms);
   return cudaGetLastError();
 }
 

@@ -25,8 +25,12 @@
 // threads before it, adds c2^(v+1) carry to its first kfix columns, and
 // stores them.  The carry into a CTA's first column is the recurrence run over
 // khalo columns to its left (the exact boundary value psi(-a, t) for the first
-// CTA).  A grid-wide barrier with a bounded wait separates rows, so every read
-// of rows n-1, n-D and n-D-1 is complete.
+// CTA).  Rows are not separated by a grid barrier: before row n a CTA waits
+// (bounded) only until the CTAs it reads have completed the rows it reads from
+// them, and until the CTAs that read it no longer need the ring slot of row n
+// (RowDeps in fdtd_internal.cuh); the ring holds D + 2 + kRowSlack rows.  The
+// per-row norm is summed from the CTAs' partials by a separate kernel after the
+// launch, in a fixed order.
 //
 // The delay term needs psi[n-D][m-D-1] + psi[n-D][m-D] and the same pair on
 // row n-D-1; the latter is the former of the previous row, so each column's
@@ -37,8 +41,7 @@
 // sources collapse to R1(n) [E(r2) - E(r2+D)] + R2(n) phi(r2), r2 = n - m - D/2,
 // E(r) = theta(r) e(r delta), with the bracket tabulated (detab).
 //
-// The ring holds D+2 rows (slot n % (D+2)); loads of ring rows written in this
-// launch bypass L1 (ld.global.cg).
+// The ring holds R = D+2+kRowSlack rows (slot n % R).
 #include <cuda_runtime.h>
 
 #include "fdtd_internal.cuh"
@@ -49,8 +52,8 @@ __device__ __forceinline__ cd ldcg(const cd* p) {
   double2 v = __ldcg(reinterpret_cast<const double2*>(p));
   return cd{v.x, v.y};
 }
-// ring rows written before the last grid barrier: cached in L1 (the barrier's
-// acquire fence discards stale lines, as after a grid-wide sync)
+// ring rows completed before this row's wait: cached in L1 (the wait's acquire
+// and fence order them before every later load of the CTA)
 __device__ __forceinline__ cd ldring(const cd* p) {
   double2 v = __ldca(reinterpret_cast<const double2*>(p));
   return cd{v.x, v.y};
@@ -66,7 +69,9 @@ __device__ __forceinline__ void stcg(cd* p, cd v) {
 // psi at x = c delta <= -a, t = r delta: C phi((c-r) delta) e(r delta)
 __device__ __forceinline__ cd psi_left(const MarchArgs& A, int64_t r, int64_t c) {
   const int Dh = A.D >> 1;
-  return A.C * (ldro(&A.phitab[r - c - Dh]) * ldro(&A.etab[r]));
+  cd v = ldro(&A.phitab[r - c - Dh]) * ldro(&A.etab[r]);
+  if (A.phitab2) v = cfma(ldro(&A.phitab2[r - c - Dh]), ldro(&A.etab2[r]), v);  // second photon of a pair
+  return A.C * v;
 }
 
 // psi at any earlier point the update of row n reads (rows n-D-1 .. n-1, or
@@ -104,6 +109,7 @@ __device__ __noinline__ cd rhs_general(const MarchArgs& A, int64_t n, int nslot,
     cd br = psi_any(A, n, nslot, r2, -m) + psi_any(A, n, nslot, r2, -m + 1);
     r = cfma(A.gs, w * (bl - br), r);
     r = cfma(R2, ldro(&A.phitab[r2]), r);  // line 4: phi((m-n) delta) = phitab[r2]
+    if (A.phitab2) r = cfma(ldro(&A.rowscal2[2 * n + 1]), ldro(&A.phitab2[r2]), r);
   }
   if (m >= Dh + 1) {  // line 3, theta(x - a)
     const int64_t r3 = n - m + Dh;
@@ -126,6 +132,7 @@ struct RowCtx {
   cd* row0;         // row n
   cd* snap;         // snapshot row or null
   cd R1, R2;
+  cd R1b, R2b;      // second term of a photon pair
   cd* hs;           // shared pair sums (null: no reuse), indexed j - hbase
   int64_t hbase;
   bool cold;        // first row of this launch: pair sums not yet in shared memory
@@ -151,6 +158,10 @@ __device__ __forceinline__ cd rhs_bulk_q(const MarchArgs& A, const RowCtx& R, in
   if (i >= 0) {
     r = cfma(R.R1, ldro(&A.detab[i]), r);
     if (i >= D) r = cfma(R.R2, ldro(&A.phitab[i - D]), r);
+    if (A.detab2) {
+      r = cfma(R.R1b, ldro(&A.detab2[i]), r);
+      if (i >= D) r = cfma(R.R2b, ldro(&A.phitab2[i - D]), r);
+    }
   }
   return r;
 }
@@ -183,40 +194,6 @@ __device__ __forceinline__ void finalize(const RowCtx& R, int64_t j, cd y, doubl
   nacc = fma(y.im, y.im, nacc);
 }
 
-// Grid-wide barrier with a bounded wait.  Returns false if any CTA has
-// latched an error (its own timeout included).
-__device__ bool grid_barrier(SyncWords* s, long long spin_cycles, int64_t row) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned int* gen = &s->bar_gen;
-    unsigned int my = *gen;
-    __threadfence();
-    unsigned int prev = atomicAdd(&s->bar_count, 1u);
-    int ok = 1;
-    if (prev == gridDim.x - 1) {
-      atomicExch(&s->bar_count, 0u);
-      __threadfence();
-      atomicAdd(&s->bar_gen, 1u);
-    } else {
-      long long t0 = clock64();
-      while (*gen == my) {
-        if (clock64() - t0 > spin_cycles) {
-          if (atomicCAS(&s->status, 0u, (unsigned)FDTD_ERR_TIMEOUT) == 0u) s->where = row;
-          ok = 0;
-          break;
-        }
-        __nanosleep(100);
-      }
-    }
-    __threadfence();
-    if (*(volatile unsigned int*)&s->status != 0u) ok = 0;
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
 __global__ void __launch_bounds__(kMarchThreads, 1) k_march_f64(const MarchArgs A) {
   constexpr int P = kMarchP;
   extern __shared__ cd s_h[];  // pair sums, khalo + CTA range entries
@@ -225,6 +202,7 @@ __global__ void __launch_bounds__(kMarchThreads, 1) k_march_f64(const MarchArgs 
   __shared__ cd s_carry;
   __shared__ cd s_halo[kMaxTrunc];
   __shared__ double s_red[kMarchThreads / 32];
+  __shared__ int s_ok;
 
   const int tid = threadIdx.x;
   const int D = A.D, Dh = D >> 1;
@@ -254,17 +232,42 @@ __global__ void __launch_bounds__(kMarchThreads, 1) k_march_f64(const MarchArgs 
   s_len[tid] = (int)(s1 - s0);
   __syncthreads();
 
-  for (int64_t n = A.n_begin; n < A.n_end; ++n) {
+  if (tid == 0) s_ok = (*(volatile unsigned int*)&A.sync->status == 0u) ? 1 : 0;
+  __syncthreads();
+  if (!s_ok) return;
+
+  int slot = (int)(A.n_begin % A.R);  // ring slot of row n
+  int64_t snap_ctr = -1, snap_idx = 0;  // row n is a snapshot row when snap_ctr == 0
+  if (A.snaps && A.tstep >= 0) {
+    snap_ctr = A.n_begin % (A.tstep + 1);
+    snap_idx = A.n_begin / (A.tstep + 1) + (snap_ctr ? 1 : 0);
+  }
+  for (int64_t n = A.n_begin; n < A.n_end; ++n,
+               slot = (slot + 1 == A.R) ? 0 : slot + 1,
+               snap_idx += (snap_ctr == 0) ? 1 : 0,
+               snap_ctr = (snap_ctr < 0) ? -1 : (snap_ctr == A.tstep ? 0 : snap_ctr + 1)) {
+    // the rows this CTA reads are complete and the ring slot of row n is free
+    if (tid < 32) {
+      const bool ok = row_wait_warp(A.deps, A.sync, A.spin_cycles, A.n_begin, blockIdx.x, n, kRowSlack);
+      if (tid == 0) s_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_ok) return;
+
     RowCtx R;
     R.n = n;
-    R.nslot = (int)(n % A.R);
-    R.row1 = A.ring + ((n - 1) % A.R) * A.stride;
-    R.rowD = (n >= D) ? A.ring + ((n - D) % A.R) * A.stride : nullptr;
-    R.rowD1 = (n >= D + 1) ? A.ring + ((n - D - 1) % A.R) * A.stride : nullptr;
-    R.row0 = A.ring + (n % A.R) * A.stride;
-    R.snap = (A.snaps && A.tstep >= 0 && n % (A.tstep + 1) == 0) ? A.snaps + (n / (A.tstep + 1)) * A.nx : nullptr;
+    // ring slots and the snapshot row from running counters (no 64-bit division per row)
+    auto back = [&](int k) { const int t = slot - k; return t < 0 ? t + A.R : t; };
+    R.nslot = slot;
+    R.row1 = A.ring + (int64_t)back(1) * A.stride;
+    R.rowD = (n >= D) ? A.ring + (int64_t)back(D) * A.stride : nullptr;
+    R.rowD1 = (n >= D + 1) ? A.ring + (int64_t)back(D + 1) * A.stride : nullptr;
+    R.row0 = A.ring + (int64_t)slot * A.stride;
+    R.snap = (snap_ctr == 0) ? A.snaps + snap_idx * A.nx : nullptr;
     R.R1 = ldro(&A.rowscal[2 * n]);
     R.R2 = ldro(&A.rowscal[2 * n + 1]);
+    R.R1b = A.rowscal2 ? ldro(&A.rowscal2[2 * n]) : cd{0.0, 0.0};
+    R.R2b = A.rowscal2 ? ldro(&A.rowscal2[2 * n + 1]) : cd{0.0, 0.0};
     R.hs = A.hreuse ? s_h : nullptr;
     R.hbase = h0;
     R.cold = (n == A.n_begin);
@@ -337,7 +340,7 @@ __global__ void __launch_bounds__(kMarchThreads, 1) k_march_f64(const MarchArgs 
       double t = 0.0;
       for (int w = 0; w < kMarchThreads / 32; ++w) t += s_red[w];
       if (j_hi == A.nx && j_lo < j_hi) t -= 0.5 * cabs2(ldcg(R.row0 + A.nx - 1));  // trapezoid end weight
-      A.partials[(n & 1) * gridDim.x + blockIdx.x] = t;
+      A.partials[(n - A.n_begin) * gridDim.x + blockIdx.x] = t;
     }
     // probes of row n in this CTA's columns (its stores of row n are complete)
     if (A.probe_off && tid < 32) {
@@ -350,12 +353,10 @@ __global__ void __launch_bounds__(kMarchThreads, 1) k_march_f64(const MarchArgs 
         }
       }
     }
-    if (!grid_barrier(A.sync, A.spin_cycles, n)) return;
-    if (blockIdx.x == 0 && tid == 0) {
-      const double* pp = A.partials + (n & 1) * gridDim.x;
-      double t = 0.5 * cabs2(psi_left(A, n, -Dh));
-      for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(pp + b);
-      A.norms[n] = A.delta * t;
+    __syncthreads();  // row n's stores (and probes) of this CTA are issued
+    if (tid == 0) {
+      __threadfence();
+      st_release_u64(&A.deps.done[blockIdx.x], (unsigned long long)(n + 1));
     }
   }
 }

@@ -86,8 +86,9 @@ __global__ void __launch_bounds__(kMeasThreads) k_measures(const cd* __restrict_
 
 // chi(x1, x2, t) of Eq. 2 from the probes and the exact boundary, one thread per point
 __global__ void k_chi(const ChiRec* __restrict__ recs, int64_t count, const double2* __restrict__ probe_val,
-                      const cd* __restrict__ phitab, const cd* __restrict__ etab, double C, double gamma,
-                      int incident, double2* __restrict__ out) {
+                      const cd* __restrict__ phitab, const cd* __restrict__ etab, const cd* __restrict__ phitab2,
+                      const cd* __restrict__ etab2, double C, double gamma, int incident,
+                      double2* __restrict__ out) {
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= count) return;
   const ChiRec& r = recs[q];
@@ -98,21 +99,29 @@ __global__ void k_chi(const ChiRec* __restrict__ recs, int64_t count, const doub
       const double2 p = probe_val[r.idx[t]];
       v = cd{p.x, p.y};
     } else if (r.kind[t] == 2) {
-      v = C * (phitab[r.idx[t]] * etab[r.row[t]]);
+      v = phitab[r.idx[t]] * etab[r.row[t]];
+      if (phitab2) v = v + phitab2[r.idx[t]] * etab2[r.row[t]];  // second photon of a pair
+      v = C * v;
     }
     sum = sum + r.w[t] * v;
   }
   cd c0 = cd{0.0, 0.0};
-  if (incident && r.phi1 >= 0 && r.phi2 >= 0) c0 = phitab[r.phi1] * phitab[r.phi2];
+  if (incident && r.phi1 >= 0 && r.phi2 >= 0) {
+    if (phitab2)  // (A/sqrt2)[phi1(x1-t) phi2(x2-t) + phi1(x2-t) phi2(x1-t)]: phitab2 = phi1, phitab = phi2
+      c0 = (C * M_SQRT1_2) * (phitab2[r.phi1] * phitab[r.phi2] + phitab2[r.phi2] * phitab[r.phi1]);
+    else
+      c0 = phitab[r.phi1] * phitab[r.phi2];
+  }
   const cd v = c0 - (0.5 * sqrt(gamma)) * sum;
   out[q] = make_double2(v.re, v.im);
 }
 
 cudaError_t launch_chi(const ChiRec* recs, int64_t count, const double2* probe_val, const cd* phitab, const cd* etab,
-                       double C, double gamma, bool incident, double2* out, cudaStream_t s) {
+                       const cd* phitab2, const cd* etab2, double C, double gamma, bool incident, double2* out,
+                       cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  k_chi<<<(unsigned)((count + 127) / 128), 128, 0, s>>>(recs, count, probe_val, phitab, etab, C, gamma,
-                                                        incident ? 1 : 0, out);
+  k_chi<<<(unsigned)((count + 127) / 128), 128, 0, s>>>(recs, count, probe_val, phitab, etab, phitab2, etab2, C,
+                                                        gamma, incident ? 1 : 0, out);
   return cudaGetLastError();
 }
 

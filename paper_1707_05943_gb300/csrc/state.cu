@@ -29,14 +29,14 @@ namespace {
 
 constexpr uint32_t kStateMagic = 0x53544446u;  // "FDTS"
 constexpr uint32_t kStateVersion = 1;
-constexpr size_t kStateHeaderBytes = 128;
+constexpr size_t kStateHeaderBytes = 256;
 
 struct StateHeader {
   uint32_t magic, version;
   int32_t precision, D;
   int64_t nx, nt, rows_done, rows_kept, lo_elems;
   int32_t elem_bytes, init_cond;
-  double delta, gamma, omega0, k, alpha, sigma, center;
+  double delta, gamma, omega0, k, alpha, sigma, center, k2, alpha2;
 };
 static_assert(sizeof(StateHeader) <= kStateHeaderBytes, "state header");
 
@@ -125,6 +125,8 @@ fdtd_status state_readout(fdtd_plan_s* P, int inst, void* dst, int64_t dst_bytes
   h.alpha = v.p->alpha;
   h.sigma = v.p->sigma;
   h.center = v.p->center;
+  h.k2 = v.p->k2;
+  h.alpha2 = v.p->alpha2;
   memcpy(hb, &h, sizeof h);
   char* d = static_cast<char*>(dst);
   cudaError_t e = cudaMemcpyAsync(d, hb, kStateHeaderBytes, cudaMemcpyDefault, s);
@@ -160,7 +162,8 @@ fdtd_status state_restore(fdtd_plan_s* P, const void* blob, int64_t nbytes, cuda
     if (h.magic != kStateMagic || h.version != kStateVersion || h.precision != p.precision || h.D != p.D ||
         h.nx != p.nx || h.nt != p.nt || h.init_cond != p.init_cond || h.elem_bytes != (int32_t)v.elem ||
         h.lo_elems != v.lo_elems || h.delta != p.delta || h.gamma != p.gamma || h.omega0 != p.omega0 ||
-        h.k != p.k || h.alpha != p.alpha || h.sigma != p.sigma || h.center != p.center)
+        h.k != p.k || h.alpha != p.alpha || h.sigma != p.sigma || h.center != p.center || h.k2 != p.k2 ||
+        h.alpha2 != p.alpha2)
       return FDTD_ERR_INVALID_ARG;
     if (h.rows_done < 1 || h.rows_done > p.nt || h.rows_kept != rows_kept(v, h.rows_done))
       return FDTD_ERR_INVALID_ARG;

@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "libfdtd.so")
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_BOUNDS, ERR_NOT_CONVERGED, \
     ERR_STATE = range(9)
 F64, F32_COMP, F64_DW = 0, 1, 2
-IC_STIM_EMISSION, IC_TWO_PHOTON_EXP, IC_TWO_PHOTON_GAUSS = 2, 3, 4
+IC_PLANE_WAVE, IC_STIM_EMISSION, IC_TWO_PHOTON_EXP, IC_TWO_PHOTON_GAUSS, IC_TWO_PHOTON_PAIR = 1, 2, 3, 4, 5
 BOUNDARY_ANALYTIC, BOUNDARY_TABLE, BOUNDARY_RESTORE = 0, 1, 2
 READ_ROW, READ_NORMS, READ_SNAPSHOTS, READ_ETABLE, READ_ROWS_DONE, READ_MEASURES, READ_STATE, READ_PROBES, \
     READ_CHI = range(9)
@@ -56,6 +56,8 @@ class FdtdParams(ctypes.Structure):
         ("rows_per_launch", ctypes.c_int32),
         ("cluster_ctas", ctypes.c_int32),
         ("mid_weight", ctypes.c_int32),
+        ("k2", ctypes.c_double),
+        ("alpha2", ctypes.c_double),
         ("max_probes", ctypes.c_int64),
         ("spin_cycles", ctypes.c_int64),
     ]
@@ -296,6 +298,8 @@ class Config:
     rows_per_launch: int = 0
     cluster_ctas: int = 0
     mid_weight: int = 0
+    k2: float = 0.0
+    alpha2: float = 0.0
     max_probes: int = 0
     spin_cycles: int = 0
 

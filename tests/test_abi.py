@@ -55,7 +55,7 @@ def _cfg(F, **kw):
 
 
 @pytest.mark.parametrize("kw", [dict(D=7), dict(D=0), dict(nx=6), dict(nt=0), dict(delta=0.0), dict(gamma=-1.0),
-                                dict(init_cond=1), dict(init_cond=3, alpha=0.0), dict(init_cond=4, sigma=0.0),
+                                dict(init_cond=0), dict(init_cond=6), dict(init_cond=5, alpha2=0.0), dict(init_cond=3, alpha=0.0), dict(init_cond=4, sigma=0.0),
                                 dict(tstep=-2), dict(cluster_ctas=9), dict(cluster_ctas=-1), dict(mid_weight=-3),
                                 dict(mid_weight=5000), dict(precision=1, cluster_ctas=9), dict(spin_cycles=-1),
                                 dict(precision=1, spin_cycles=-5)])
@@ -65,6 +65,15 @@ def test_plan_rejects_bad_params(F, kw):
     st = L.fdtd_plan(ctypes.byref(_cfg(F, **kw)), 1, None, ctypes.byref(ws), ctypes.byref(plan))
     assert st == F.ERR_INVALID_ARG
     assert not plan.value
+
+
+def test_complex64_photon_pair_is_unsupported(F):
+    # two different photons are marched by the FP64-accurate plans only
+    L = F.lib()
+    ws, plan = ctypes.c_size_t(), ctypes.c_void_p()
+    st = L.fdtd_plan(ctypes.byref(_cfg(F, precision=1, init_cond=5, alpha2=1.0)), 1, None, ctypes.byref(ws),
+                     ctypes.byref(plan))
+    assert st == F.ERR_UNSUPPORTED and not plan.value
 
 
 def test_plan_rejects_wrong_struct_size(F):

@@ -35,23 +35,27 @@ def detector_points(w, taus, rows):
 
 
 @pytest.mark.parametrize("prec", [0, 2], ids=["f64", "dw"])
-@pytest.mark.parametrize("kind", ["exp", "gauss"])
+@pytest.mark.parametrize("kind", ["exp", "gauss", "pair", "plane"])
 def test_chi_matches_oracle(F, oracle, prec, kind):
     if kind == "exp":
         w = W.jittered(W.exp_pair(400, 1000, D=20, a=0.5), seed=3, n=1)[0]
-    else:
+    elif kind == "gauss":
         w = W.gauss_pair(400, 1000, D=20, a=0.5, gamma=1.0, k0a=0.25 * math.pi, sigma=1.0, lead=4.0)
+    elif kind == "pair":
+        w = W.photon_pair(400, 1000, D=20, a=0.5, dk1=0.4, alpha1=0.8, dk2=-0.3, alpha2=1.5)
+    else:
+        w = W.plane_wave(400, 1000, D=20, a=0.5, dk=0.2)
     pts = detector_points(w, taus=list(range(0, 60, 3)), rows=list(range(150, 1000, 70)))
     s = F.Solver(F.Config(nx=w.nx, nt=w.nt, D=w.D, delta=w.delta, gamma=w.gamma, omega0=w.omega0, k=w.k,
-                          init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center, tstep=-1,
-                          precision=prec, max_probes=4 * len(pts), rows_per_launch=300))
+                          init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center, k2=w.k2,
+                          alpha2=w.alpha2, tstep=-1, precision=prec, max_probes=4 * len(pts), rows_per_launch=300))
     s.set_boundary()
     F.fdtd_set_chi_points(s.plan, pts)
     s.march(w.nt)
     got = s.read(F.READ_CHI)
     s.close()
     p = oracle.Params(nx=w.nx, nt=w.nt, D=w.D, delta=w.delta, gamma=w.gamma, omega0=w.omega0, k=w.k,
-                      init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center)
+                      init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center, k2=w.k2, alpha2=w.alpha2)
     grid = oracle.march(p, tstep=0)["snaps"]
     want = oracle.chi(p, grid, pts)
     assert np.max(np.abs(got - want)) <= 1e-12 * np.abs(want).max(), np.max(np.abs(got - want))

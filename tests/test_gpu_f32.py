@@ -85,7 +85,8 @@ def test_batch_of_uneven_instances(F, oracle):
           W.gauss_pair(1500, 1200, D=60, a=1.5, gamma=1.0, k0a=1.1, sigma=0.8),
           W.Workload("stim", 512, 700, 10, 0.2, 1.3, 2.0, 2.0, 2, alpha=0.7),
           W.jittered(W.exp_pair(333, 500, D=12, a=0.3), seed=3, n=1)[0],
-          W.gauss_pair(4097, 800, D=200, a=4.0, gamma=0.5, k0a=2.5, sigma=3.0)]
+          W.gauss_pair(4097, 800, D=200, a=4.0, gamma=0.5, k0a=2.5, sigma=3.0),
+          W.plane_wave(900, 1000, D=30, a=0.75, dk=0.3)]
     res = run_batch(F, ws)
     for w, (snaps, norms) in zip(ws, res):
         r = oracle.march(oparams(oracle, w), tstep=0)

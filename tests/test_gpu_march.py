@@ -30,14 +30,15 @@ def F():
 
 def cfg_of(F, w, **kw):
     base = dict(nx=w.nx, nt=w.nt, D=w.D, delta=w.delta, gamma=w.gamma, omega0=w.omega0, k=w.k,
-                init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center, tstep=0)
+                init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center, k2=w.k2, alpha2=w.alpha2,
+                tstep=0)
     base.update(kw)
     return F.Config(**base)
 
 
 def oparams(O, w):
     return O.Params(nx=w.nx, nt=w.nt, D=w.D, delta=w.delta, gamma=w.gamma, omega0=w.omega0, k=w.k,
-                    init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center)
+                    init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center, k2=w.k2, alpha2=w.alpha2)
 
 
 def run_gpu(F, w, pieces=None, **kw):
@@ -105,6 +106,23 @@ def test_stimulated_emission(F, oracle, prec):
 @PREC
 def test_gaussian_pair(F, oracle, prec):
     w = W.gauss_pair(600, 1500, D=40, a=1.0, gamma=1.0, k0a=0.3 * math.pi, sigma=1.0)
+    check_parity(F, oracle, w, precision=prec)
+
+
+@PREC
+@pytest.mark.parametrize("dk", [0.0, 0.4])
+def test_plane_wave(F, oracle, prec, dk):
+    # Sec. 2 (a): two-photon plane wave, e0 through gamma(n, z) with p = k - w0 + i Gamma/2
+    w = W.plane_wave(700, 1600, D=40, dk=dk)
+    check_parity(F, oracle, w, precision=prec)
+
+
+@PREC
+@pytest.mark.parametrize("dk1,a1,dk2,a2", [(0.3, 0.7, -0.5, 1.4), (0.0, 1.0, 0.0, 1.0)])
+def test_two_different_photons(F, oracle, prec, dk1, a1, dk2, a2):
+    # Sec. 2 (c) with (k1, alpha1) != (k2, alpha2): the boundary is the sum of two
+    # separable terms; (0, 1, 0, 1) is the identical pair through the same path
+    w = W.photon_pair(900, 1500, D=40, dk1=dk1, alpha1=a1, dk2=dk2, alpha2=a2)
     check_parity(F, oracle, w, precision=prec)
 
 
@@ -208,11 +226,10 @@ def test_call_order_and_buffer_errors(F):
 
 @PREC
 def test_wait_timeout_latches_status(F, prec):
-    # a wait limit of one cycle: in FDTD_F64 every CTA that is not the last to reach
-    # a row's grid barrier gives up at once; in FDTD_F64_DW a CTA whose left
-    # neighbour has not yet published the previous row does.  Either latches
-    # FDTD_ERR_TIMEOUT and returns; no wait is left running, and the readout
-    # reports the status instead of data
+    # a wait limit of one cycle: a CTA whose left neighbour has not yet published
+    # the previous row gives up at once, latches FDTD_ERR_TIMEOUT and returns; the
+    # others see the latched status in their own waits and return too.  No wait is
+    # left running, and the readout reports the status instead of data
     import ctypes
     w = W.exp_pair(20011, 64, D=40)
     s = F.Solver(cfg_of(F, w, tstep=-1, spin_cycles=1, precision=prec))

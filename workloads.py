@@ -27,10 +27,13 @@ class Workload:
     gamma: float
     omega0: float
     k: float
-    init_cond: int     # 2 stimulated emission, 3 two exponential photons, 4 two Gaussian photons
+    init_cond: int     # 1 plane wave, 2 stimulated emission, 3 two identical exponential photons,
+                       # 4 two identical Gaussian photons, 5 two different exponential photons
     alpha: float = 1.0
     sigma: float = 0.0
     center: float = 0.0
+    k2: float = 0.0       # init_cond 5: the second photon's carrier and width
+    alpha2: float = 0.0
 
     @property
     def a(self) -> float:
@@ -49,6 +52,19 @@ def exp_pair(nx, nt, D=40, a=1.0, gamma=1.0, k0a=PI / 2, alpha=1.0, name="exp") 
     """Two identical exponential photons of width 1/(alpha Gamma) (Sec. 2 (c))."""
     w0 = k0a / a
     return Workload(name, nx, nt, D, 2 * a / D, gamma, w0, w0, 3, alpha=alpha)
+
+
+def plane_wave(nx, nt, D=40, a=1.0, gamma=1.0, k0a=PI / 2, dk=0.0, name="plane") -> Workload:
+    """Two-photon plane wave e^{ik(x1+x2)} (Sec. 2 (a)), k = w0 + dk."""
+    w0 = k0a / a
+    return Workload(name, nx, nt, D, 2 * a / D, gamma, w0, w0 + dk, 1)
+
+
+def photon_pair(nx, nt, D=40, a=1.0, gamma=1.0, k0a=PI / 2, dk1=0.0, alpha1=1.0, dk2=0.0, alpha2=1.0,
+                name="pair") -> Workload:
+    """Two different exponential photons (k1, alpha1), (k2, alpha2) (Sec. 2 (c)), k_i = w0 + dk_i."""
+    w0 = k0a / a
+    return Workload(name, nx, nt, D, 2 * a / D, gamma, w0, w0 + dk1, 5, alpha=alpha1, k2=w0 + dk2, alpha2=alpha2)
 
 
 def gauss_pair(nx, nt, D, a, gamma, k0a, sigma, lead=8.0, name="gauss") -> Workload:
