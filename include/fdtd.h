@@ -31,9 +31,9 @@
  *
  * Streams and errors.  Every call returns an fdtd_status; nothing throws or
  * exits.  Work is queued on the plan's stream; fdtd_readout synchronises it.
- * Device-side failures (a bounded wait that gave up, an index outside a
- * buffer) latch a status word in the workspace that the next fdtd_readout
- * returns.  Plans are not thread-safe; use one plan per stream.
+ * Device-side failures (a bounded wait that gave up, a boundary series that
+ * did not converge) latch a status word in the workspace that the next
+ * fdtd_readout returns.  Plans are not thread-safe; use one plan per stream.
  * Call order: fdtd_plan -> fdtd_bind_workspace -> fdtd_set_boundary ->
  * fdtd_march* -> fdtd_readout*; out-of-order calls return FDTD_ERR_STATE.
  */
@@ -56,7 +56,8 @@ typedef enum {
   FDTD_ERR_WORKSPACE = 3,     /* workspace missing, too small or misaligned        */
   FDTD_ERR_CUDA = 4,          /* a CUDA runtime call failed                        */
   FDTD_ERR_TIMEOUT = 5,       /* a device-side bounded wait gave up                */
-  FDTD_ERR_BOUNDS = 6,        /* a device-side index check failed                  */
+  FDTD_ERR_BOUNDS = 6,        /* reserved: no call of this build returns it (every */
+                              /* index a kernel uses is checked on the host first)  */
   FDTD_ERR_NOT_CONVERGED = 7, /* a boundary series or quadrature did not converge  */
   FDTD_ERR_STATE = 8          /* call out of order                                 */
 } fdtd_status;
@@ -222,7 +223,8 @@ fdtd_status fdtd_march_graph(fdtd_plan_t plan, int64_t n_rows);
  * fdtd_readout -- synchronise the plan's stream and copy `kind` into dst.
  *   dst       : caller-owned host or device memory (cudaMemcpyDefault).
  *   dst_bytes : capacity of dst; FDTD_ERR_INVALID_ARG if too small.
- * Returns a latched device error (FDTD_ERR_TIMEOUT / FDTD_ERR_BOUNDS) first.
+ * Returns a latched device error (FDTD_ERR_TIMEOUT, FDTD_ERR_NOT_CONVERGED)
+ * first.
  * Norms: N(n) = delta * trapezoid of |psi(x, n delta)|^2 over x = -a (exact
  * boundary value) .. the last marched column, accumulated in FP64 (App. D).
  */

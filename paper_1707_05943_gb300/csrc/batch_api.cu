@@ -214,6 +214,7 @@ fdtd_status batch_set_boundary(fdtd_plan_s* P, int32_t source, const void* table
       if (e != cudaSuccess) return cuda_fail(P, e, "cudaMemcpyAsync(table)");
     }
     fdtd::BoundaryArgs a;
+    memset(&a, 0, sizeof a);  // no second photon: the pair fields stay null
     a.etab = at<cd>(P, b.off_etab);
     a.phitab = at<cd>(P, b.off_phi);
     a.rowscal = at<cd>(P, b.off_rowscal);
