@@ -105,10 +105,15 @@ typedef struct {
   double center;         /* Gaussian centre x_c (IC 4); the pulse is cut at x=-a */
   int32_t tstep;         /* keep every (tstep+1)-th row as a snapshot; -1: none  */
   int32_t rows_per_launch; /* rows marched per kernel launch; 0 = default        */
-  int32_t cluster_ctas;  /* FDTD_F32_COMP: CTAs of the thread-block cluster that  */
-                         /* marches a wide instance, 1..8; 0 = by the widest one  */
-  int32_t mid_weight;    /* column split: cost of a column of -a < x <= 3a in     */
-                         /* bulk columns, 1..4096; 0 = 16                          */
+  int32_t cluster_ctas;  /* FDTD_F32_COMP: most band streams of one instance,    */
+                         /* 1..64 (0 = 32): an instance marches in bands of 256  */
+                         /* rows, g streams of them in flight at once            */
+  int32_t mid_weight;    /* FDTD_F64, FDTD_F64_DW: cost of a column of            */
+                         /* -a < x <= 3a in bulk columns in the column split.     */
+                         /* FDTD_F32_COMP: stream share s: instance i gets        */
+                         /* g = ceil(nx_i nt_i / (sum nx nt / (CTAs s/8))) band   */
+                         /* streams, capped by cluster_ctas and its bands.        */
+                         /* 1..4096; 0 = 16                                        */
   double k2;             /* FDTD_IC_TWO_PHOTON_PAIR: carrier of the second photon */
   double alpha2;         /* FDTD_IC_TWO_PHOTON_PAIR: its width (> 0)             */
   int64_t max_probes;    /* FDTD_F64 / FDTD_F64_DW: capacity of fdtd_set_probes;  */
@@ -162,7 +167,8 @@ enum {
  *                  plans hold 1 or more independent instances (each with its own
  *                  nx, nt, D, physics and tstep; rows_per_launch, cluster_ctas
  *                  and mid_weight are taken from p[0]); fdtd_march then advances every instance by n_rows in
- *                  one persistent launch, a thread-block cluster per instance.
+ *                  one persistent cooperative launch: an instance is marched in
+ *                  bands of 256 rows, up to cluster_ctas band streams at once.
  *   cuda_stream  : cudaStream_t the plan queues its work on (NULL = default).
  *   workspace_bytes (out): device bytes the caller must lend (256-byte aligned).
  *   out (out)    : new plan handle, released by fdtd_destroy.

@@ -1,12 +1,15 @@
 """Autotuner of complex64 batched plans.
 
 Two plan knobs change how a batch maps onto the GPU without changing what it
-computes beyond FP32 rounding order:
+computes (the march's results do not depend on them, bit for bit):
 
-* ``cluster_ctas`` -- CTAs of the thread-block cluster that marches one wide
-  instance (more CTAs: shorter rows per CTA, fewer instances in flight);
-* ``mid_weight``  -- the cost, in bulk columns, given to a column of the region
-  -a < x <= 3a when a cluster's columns are split over its CTAs.
+* ``cluster_ctas`` -- the most band streams of one instance: an instance is
+  marched in bands of 256 rows, up to that many in flight at once (the depth of
+  the temporal blocking; its ring grows by 256 rows per stream);
+* ``mid_weight`` -- the stream share s: instance i gets one stream per
+  total / (CTAs s/8) updates of its own.  A larger share splits mid-sized
+  instances into more streams (shorter time to finish, more ring memory); a
+  smaller one keeps more CTAs on separate instances.
 
 ``tune`` estimates the whole march's time for every candidate pair and keeps
 the fastest, caching the choice per batch shape in a JSON file.  A batch's
@@ -30,7 +33,7 @@ from dataclasses import dataclass
 
 from . import fdtd as F
 
-CANDIDATES = tuple((c, w) for c in (2, 4, 8) for w in (4, 8, 16, 32))
+CANDIDATES = tuple((c, w) for c in (8, 16, 32) for w in (8, 16, 32))
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 
@@ -71,7 +74,7 @@ def _save(path, cache):
     os.replace(tmp, path)
 
 
-def time_march(configs, cluster_ctas: int, mid_weight: int, rows: int = 256, warm: int = 1024) -> float:
+def time_march(configs, cluster_ctas: int, mid_weight: int, rows: int = 1024, warm: int = 1024) -> float:
     """Milliseconds for `rows` rows of the batch's march after `warm` rows (CUDA events)."""
     import torch
     cfgs = []
@@ -111,7 +114,7 @@ def time_march(configs, cluster_ctas: int, mid_weight: int, rows: int = 256, war
         del buf
 
 
-def estimate_march(configs, cluster_ctas: int, mid_weight: int, rows: int = 256, phases: int = 4) -> float:
+def estimate_march(configs, cluster_ctas: int, mid_weight: int, rows: int = 1024, phases: int = 4) -> float:
     """Estimated milliseconds of the whole march: per quarter of the row range,
     the time of `rows` rows of the instances still marching there, scaled by
     the quarter's length."""
@@ -129,7 +132,7 @@ def estimate_march(configs, cluster_ctas: int, mid_weight: int, rows: int = 256,
     return total
 
 
-def tune(configs, rows: int = 256, candidates=CANDIDATES, cache_path: str | None = DEFAULT_CACHE,
+def tune(configs, rows: int = 1024, candidates=CANDIDATES, cache_path: str | None = DEFAULT_CACHE,
          timer=None, refresh: bool = False) -> Choice:
     """The fastest (cluster_ctas, mid_weight) for this batch shape, from the
     cache when present (and not `refresh`), else measured with `timer`

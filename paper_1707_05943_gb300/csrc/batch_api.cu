@@ -39,31 +39,12 @@ fdtd_status cuda_fail(fdtd_plan_s* p, cudaError_t e, const char* where) {
   return FDTD_ERR_CUDA;
 }
 
-constexpr int kMidWeight = 16;
-
-// columns of CTA `rank` of `C`, as the kernel splits them (cost-weighted)
-// the device's column split (cta_range in march_f32c.cu), to size shared memory
-void cta_range_host(int64_t nx, int D, int rank, int C, int wmid, int64_t* lo, int64_t* hi) {
-  const int64_t G2 = std::min<int64_t>(2 * (int64_t)D, nx);
-  const int64_t wm = wmid;
-  const int64_t W = wm * G2 + (nx - G2);
-  int64_t g = (2 * (int64_t)C * wm * G2 + W) / (2 * W);
-  if (g > C - 1) g = C - 1;
-  if (g >= 1 && nx > G2) {
-    if (rank < g) {
-      *lo = G2 * rank / g;
-      *hi = G2 * (rank + 1) / g;
-    } else {
-      const int64_t r = rank - g, Cb = C - g;
-      *lo = G2 + (nx - G2) * r / Cb;
-      *hi = G2 + (nx - G2) * (r + 1) / Cb;
-    }
-    return;
-  }
-  auto inv = [&](int64_t x) { return x <= wm * G2 ? (x + wm - 1) / wm : G2 + (x - wm * G2); };
-  *lo = inv(W * rank / C);
-  *hi = inv(W * (rank + 1) / C);
-}
+// gang share of complex64 plans (mid_weight): an instance is split into one band
+// stream per total / (grid share / 8) updates of its own
+constexpr int kGangShare = 16;
+constexpr int kGangDefault = 32;  // band streams of the largest instance
+constexpr int kTablePad = 64;     // zero entries after the FP32 source tables (>= 32 + prefetch distance)
+constexpr long long kSpinDefault = 4000000000LL;  // about 2 s at GB300 clocks
 
 fdtd_status validate(const fdtd_params& p) {
   if (p.struct_size != sizeof(fdtd_params)) return FDTD_ERR_INVALID_ARG;
@@ -75,7 +56,8 @@ fdtd_status validate(const fdtd_params& p) {
     return FDTD_ERR_INVALID_ARG;
   if (p.init_cond == FDTD_IC_TWO_PHOTON_GAUSS && !(p.sigma > 0)) return FDTD_ERR_INVALID_ARG;
   if (p.tstep < -1 || p.rows_per_launch < 0 || p.spin_cycles < 0) return FDTD_ERR_INVALID_ARG;
-  if (p.cluster_ctas < 0 || p.cluster_ctas > 8 || p.mid_weight < 0 || p.mid_weight > 4096) return FDTD_ERR_INVALID_ARG;
+  if (p.cluster_ctas < 0 || p.cluster_ctas > fdtd::kGangMax || p.mid_weight < 0 || p.mid_weight > 4096)
+    return FDTD_ERR_INVALID_ARG;
   if (p.precision != FDTD_F32_COMP) return FDTD_ERR_INVALID_ARG;
   return FDTD_OK;
 }
@@ -86,6 +68,19 @@ T* at(fdtd_plan_s* P, size_t off) {
 }
 
 }  // namespace
+
+fdtd::RowMap row_map(fdtd_plan_s* P, int i) {
+  const fdtd_batch_inst& b = P->inst[i];
+  fdtd::RowMap m;
+  m.ring = at<float2>(P, b.off_ring);
+  m.stride = b.stride;
+  m.skew = at<float2>(P, b.off_skew);
+  m.rd = b.p.nx - b.p.D;
+  m.nx = b.p.nx;
+  m.R = b.R;
+  m.D = b.p.D;
+  return m;
+}
 
 fdtd_status batch_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n, void* cuda_stream,
                             size_t* workspace_bytes) {
@@ -101,22 +96,26 @@ fdtd_status batch_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n, v
   cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
   P->record_errors = true;
   P->inst.assign(n, fdtd_batch_inst{});
-  // cluster size: enough CTAs that the widest instance gives each thread a few columns
-  int64_t maxnx = 0;
-  for (int i = 0; i < n; ++i) maxnx = std::max<int64_t>(maxnx, pin[i].nx);
-  int cs = 1;
-  while (cs < 8 && (int64_t)cs * fdtd::kF32Threads * 4 < maxnx) cs *= 2;
-  if (pin[0].cluster_ctas > 0) cs = pin[0].cluster_ctas;
-  P->csize = cs;
-  P->mid_weight = pin[0].mid_weight > 0 ? pin[0].mid_weight : kMidWeight;
+  // the persistent launch: every CTA resident
+  const int per_sm = fdtd::march_f32c_blocks_per_sm();
+  if (per_sm <= 0) return FDTD_ERR_CUDA;
+  P->grid = per_sm * P->num_sms;
+  // gang (band streams in flight) of each instance: its share of the work in units
+  // of total / (grid share/8), at most gang_max, at most its bands, and at most the
+  // grid (no stream may wait on one that no CTA is free to take)
+  P->gang_max = pin[0].cluster_ctas > 0 ? pin[0].cluster_ctas : kGangDefault;
+  if (P->gang_max > P->grid) P->gang_max = P->grid;
+  P->mid_weight = pin[0].mid_weight > 0 ? pin[0].mid_weight : kGangShare;
+  double utot = 0.0;
+  for (int i = 0; i < n; ++i) utot += (double)pin[i].nx * (double)pin[i].nt;
+  const double unit = utot / ((double)P->grid * P->mid_weight / 8.0);
 
   size_t off = 0;
   P->off_sync = off;  off = align_up(off + sizeof(fdtd::SyncWords));
   P->off_desc = off;  off = align_up(off + sizeof(fdtd::InstDesc) * (size_t)n);
-  P->off_order = off; off = align_up(off + sizeof(fdtd::WorkItem) * (size_t)n);
+  P->off_order = off; off = align_up(off + sizeof(fdtd::WorkItem) * (size_t)n * fdtd::kGangMax);
   P->off_queue = off; off = align_up(off + sizeof(unsigned int) * 4);
   P->off_eargs = off; off = align_up(off + sizeof(fdtd::EtabArgs) * (size_t)n);
-  int64_t cols = 0;
   for (int i = 0; i < n; ++i) {
     const fdtd_params& p = pin[i];
     fdtd_batch_inst& b = P->inst[i];
@@ -130,25 +129,20 @@ fdtd_status batch_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n, v
     b.c3 = (p.gamma / 8.0) * b.cs;
     b.gs = (-p.gamma / 4.0) * b.cs;
     b.C = (p.init_cond == FDTD_IC_STIM_EMISSION) ? 1.0 : sqrt(2.0);
-    // carry depth at FP32 rounding: |c2|^k < 2^-26
-    const double ac2 = hypot(b.c2.re, b.c2.im);
-    int k = (ac2 <= 0) ? 1 : (int)ceil(-26.0 * log(2.0) / log(ac2));
-    if (k < 1) k = 1;
-    if (ac2 >= 1.0 || k > fdtd::kF32MaxTrunc) return FDTD_ERR_UNSUPPORTED;
-    b.kfix = k;
-    b.khalo = k;
-    b.R = p.D + 2;
-    b.stride = (p.nx + 63) / 64 * 64 + 64;  // complex64 row pitch, never a power of two apart
+    // the row recurrence y_m = c2 y_{m-1} + r_m is stable only for |c2| < 1
+    if (hypot(b.c2.re, b.c2.im) >= 1.0) return FDTD_ERR_UNSUPPORTED;
+    const int64_t bands = (p.nt - 1 + fdtd::kF32Band - 1) / fdtd::kF32Band;
+    int64_t g = (int64_t)ceil((double)p.nx * (double)p.nt / unit);
+    g = std::min<int64_t>(std::min<int64_t>(g, P->gang_max), std::max<int64_t>(bands, 1));
+    b.g = (int)std::max<int64_t>(g, 1);
+    // rows an in-flight band reads: back to D + 1 below the oldest of g bands in flight
+    b.R = p.D + 2 + fdtd::kF32Band * b.g + fdtd::kRowSlack;
+    b.stride = (p.D + 31) / 32 * 32 + 32;  // inner ring row pitch (columns < D)
     b.nphi = p.nt + 3 * (int64_t)p.D + 8;
     b.nsnap = (p.tstep >= 0) ? (p.nt - 1) / (p.tstep + 1) + 1 : 0;
-    int64_t cm = 0;
-    for (int r = 0; r < cs; ++r) {
-      int64_t lo, hi;
-      cta_range_host(p.nx, p.D, r, cs, P->mid_weight, &lo, &hi);
-      cm = std::max(cm, hi - lo);
-    }
-    b.cols_max = cm + b.khalo;
-    cols = std::max(cols, b.cols_max);
+    b.dpad = (p.D + 7) / 8 * 8;
+    b.nxpad = (p.nx + 7) / 8 * 8;
+    b.lo_elems = 2 * b.dpad + b.nxpad + p.nt;
     b.off_etab = off;     off = align_up(off + sizeof(cd) * (size_t)p.nt);
     b.off_phi = off;      off = align_up(off + sizeof(cd) * (size_t)b.nphi);
     b.off_rowscal = off;  off = align_up(off + 2 * sizeof(cd) * (size_t)p.nt);
@@ -156,24 +150,24 @@ fdtd_status batch_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n, v
     b.off_norms = off;    off = align_up(off + sizeof(double) * (size_t)p.nt);
     b.off_hscr = off;     off = align_up(off + sizeof(cd) * (size_t)p.nt);
     b.off_etab32 = off;   off = align_up(off + sizeof(float2) * (size_t)p.nt);
-    b.off_phi32 = off;    off = align_up(off + sizeof(float2) * (size_t)b.nphi);
+    // FP32 source tables with a zero entry at index -1 and kTablePad zeros after the end:
+    // the sweep indexes them without bounds tests (out of the light cone they give 0)
+    b.off_phi32 = off;    off = align_up(off + sizeof(float2) * (size_t)(b.nphi + 1 + kTablePad));
     b.off_rowscal32 = off; off = align_up(off + 2 * sizeof(float2) * (size_t)p.nt);
-    b.off_detab32 = off;  off = align_up(off + sizeof(float2) * (size_t)(p.nt + p.D));
-    b.off_lo = off;       off = align_up(off + sizeof(float2) * 2 * (size_t)((p.nx + 4 + 7) / 8 * 8));
+    b.off_detab32 = off;  off = align_up(off + sizeof(float2) * (size_t)(p.nt + p.D + 1 + kTablePad));
+    b.off_lo = off;       off = align_up(off + sizeof(float2) * (size_t)b.lo_elems);
     b.off_bnd = off;      off = align_up(off + sizeof(float2) * 2 * (size_t)p.nt);
     b.off_bnorm = off;    off = align_up(off + sizeof(double) * (size_t)p.nt);
-    b.off_part = off;     off = align_up(off + sizeof(double) * 2 * fdtd::kClusterMax);
+    b.off_bsync = off;    off = align_up(off + sizeof(unsigned long long) * (1 + fdtd::kGangMax));
     b.off_ring = off;     off = align_up(off + sizeof(float2) * (size_t)b.R * (size_t)b.stride);
+    b.off_skew = off;     off = align_up(off + sizeof(float2) * (size_t)b.R * (size_t)(p.nx - p.D));
     b.off_snaps = off;    off = align_up(off + sizeof(float2) * (size_t)b.nsnap * (size_t)p.nx);
     b.rows_done = 0;
   }
-  // pair sums in shared memory when the widest CTA range fits (200 KB); otherwise
-  // the kernel reads both delay rows from L2/HBM
-  P->smem_cols = (fdtd::march_f32c_smem(cols) <= size_t(200) * 1024) ? cols : 0;
-  const size_t smem = fdtd::march_f32c_smem(P->smem_cols);
-  int maxc = fdtd::march_f32c_max_clusters(P->csize, smem);
-  if (maxc <= 0) return FDTD_ERR_CUDA;
-  P->nclusters = maxc;  // capped by the number of work items at set-up
+  // one row of the widest instance: row readouts and checkpoints gather through it
+  int64_t maxnx = 0;
+  for (int i = 0; i < n; ++i) maxnx = std::max<int64_t>(maxnx, pin[i].nx);
+  P->off_stage = off; off = align_up(off + sizeof(float2) * (size_t)maxnx);
   P->ws_need = off;
   P->state = 0;
   *workspace_bytes = off;
@@ -201,12 +195,18 @@ fdtd_status batch_set_boundary(fdtd_plan_s* P, int32_t source, const void* table
   for (int i = 0; i < n; ++i) {
     fdtd_batch_inst& b = P->inst[i];
     const fdtd_params& p = b.p;
-    e = cudaMemsetAsync(P->ws + b.off_ring, 0, sizeof(float2) * (size_t)b.R * (size_t)b.stride, s);
+    // every ring row a march reads was written by it, except row 0 (zero at x > -a)
+    e = fdtd::launch_row_move(row_map(P, i), 0, nullptr, 2, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->ws + b.off_norms, 0, sizeof(double) * (size_t)p.nt, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->ws + b.off_lo, 0, sizeof(float2) * (size_t)b.lo_elems, s);
     if (e == cudaSuccess)
-      e = cudaMemsetAsync(P->ws + b.off_lo, 0, sizeof(float2) * 2 * (size_t)((p.nx + 4 + 7) / 8 * 8), s);
+      e = cudaMemsetAsync(P->ws + b.off_bsync, 0, sizeof(unsigned long long) * (1 + fdtd::kGangMax), s);
     if (e == cudaSuccess && b.nsnap)
       e = cudaMemsetAsync(P->ws + b.off_snaps, 0, sizeof(float2) * (size_t)b.nsnap * (size_t)p.nx, s);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(P->ws + b.off_phi32, 0, sizeof(float2) * (size_t)(b.nphi + 1 + kTablePad), s);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(P->ws + b.off_detab32, 0, sizeof(float2) * (size_t)(p.nt + p.D + 1 + kTablePad), s);
     if (e != cudaSuccess) return cuda_fail(P, e, "cudaMemsetAsync");
     if (source == FDTD_BOUNDARY_TABLE) {
       e = cudaMemcpyAsync(P->ws + b.off_etab, tab, sizeof(cd) * (size_t)p.nt, cudaMemcpyDeviceToDevice, s);
@@ -261,12 +261,8 @@ fdtd_status batch_set_boundary(fdtd_plan_s* P, int32_t source, const void* table
     d.nphi = b.nphi;
     d.range[0] = 1;
     d.range[1] = 1;
-    d.smem_cols = P->smem_cols;
     d.D = p.D;
     d.R = b.R;
-    d.kfix = b.kfix;
-    d.khalo = b.khalo;
-    d.mid_weight = P->mid_weight;
     d.tstep = p.tstep;
     auto f = [](cd v) { return make_float2((float)v.re, (float)v.im); };
     auto flo = [](cd v) {  // the part of v that its FP32 rounding drops
@@ -280,25 +276,24 @@ fdtd_status batch_set_boundary(fdtd_plan_s* P, int32_t source, const void* table
     d.c2lo = flo(b.c2);
     d.c3lo = flo(b.c3);
     d.gs = f(b.gs);
-    cd pw = cd{1.0, 0.0};
-    for (int k = 0; k <= fdtd::kF32MaxTrunc; ++k) {
-      d.c2pow[k] = f(pw);
-      d.c2powlo[k] = flo(pw);
-      pw = pw * b.c2;
-    }
     d.C = b.C;
     d.delta = p.delta;
     d.ring = at<float2>(P, b.off_ring);
+    d.skew = at<float2>(P, b.off_skew);
+    d.rd = p.nx - p.D;
     d.snaps = b.nsnap ? at<float2>(P, b.off_snaps) : nullptr;
-    d.lo = at<float2>(P, b.off_lo);
-    d.lo_pitch = (p.nx + 4 + 7) / 8 * 8;
-    d.partials = at<double>(P, b.off_part);
+    d.lo_in = at<float2>(P, b.off_lo);
+    d.lo_row = d.lo_in + 2 * b.dpad;
+    d.lo_edge = d.lo_row + b.nxpad;
+    d.dpad = b.dpad;
+    d.bsync = at<unsigned long long>(P, b.off_bsync);
+    d.spin = p.spin_cycles > 0 ? (long long)p.spin_cycles : kSpinDefault;
     d.norms = at<double>(P, b.off_norms);
     d.etab = at<cd>(P, b.off_etab);
     d.phitab = at<cd>(P, b.off_phi);
     d.etab32 = at<float2>(P, b.off_etab32);
-    d.phitab32 = at<float2>(P, b.off_phi32);
-    d.detab32 = at<float2>(P, b.off_detab32);
+    d.phitab32 = at<float2>(P, b.off_phi32) + 1;
+    d.detab32 = at<float2>(P, b.off_detab32) + 1;
     d.rowscal32 = at<float2>(P, b.off_rowscal32);
     d.bnd32 = at<float2>(P, b.off_bnd);
     d.bnorm = at<double>(P, b.off_bnorm);
@@ -306,30 +301,16 @@ fdtd_status batch_set_boundary(fdtd_plan_s* P, int32_t source, const void* table
     if (e != cudaSuccess) return cuda_fail(P, e, "tables32");
     b.rows_done = 1;
   }
-  // work items, largest first: an instance wider than kSoloCols gets the whole
-  // cluster; narrower ones go one per CTA, csize to an item
-  const int64_t kSoloCols = (int64_t)fdtd::kF32Threads * 8;
+  // the queue: largest instance first, each as its g band streams in order
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    return P->inst[x].p.nx * P->inst[x].p.nt > P->inst[y].p.nx * P->inst[y].p.nt;
+    return (double)P->inst[x].p.nx * (double)P->inst[x].p.nt > (double)P->inst[y].p.nx * (double)P->inst[y].p.nt;
   });
   std::vector<fdtd::WorkItem> items;
-  for (size_t q = 0; q < order.size();) {
-    fdtd::WorkItem w;
-    memset(&w, 0, sizeof w);
-    if (P->csize == 1 || P->inst[order[q]].p.nx > kSoloCols) {
-      w.count = 1;
-      w.solo = 0;
-      w.inst[0] = order[q++];
-    } else {
-      w.solo = 1;
-      while (w.count < P->csize && q < order.size()) w.inst[w.count++] = order[q++];
-    }
-    items.push_back(w);
-  }
+  for (int i : order)
+    for (int r = 0; r < P->inst[i].g; ++r) items.push_back(fdtd::WorkItem{i, r, P->inst[i].g, 0});
   P->nitems = (int)items.size();
-  if (P->nclusters > P->nitems) P->nclusters = P->nitems;
   if (source == FDTD_BOUNDARY_RESTORE) {
     // each instance resumes at its checkpoint's row (rings, remainders, norms loaded)
     std::vector<int64_t> done(n, 1);
@@ -359,7 +340,6 @@ fdtd_status batch_march(fdtd_plan_s* P, int64_t rows) {
   if (rows <= 0) return FDTD_OK;
   const int64_t per = P->p.rows_per_launch > 0 ? P->p.rows_per_launch : 4096;
   cudaStream_t s = P->stream;
-  const size_t smem = fdtd::march_f32c_smem(P->smem_cols);
   for (int64_t done = 0; done < rows; done += per) {
     const int64_t step = std::min<int64_t>(per, rows - done);
     cudaError_t e = fdtd::launch_advance(at<fdtd::InstDesc>(P, P->off_desc), n, step, s);
@@ -367,7 +347,7 @@ fdtd_status batch_march(fdtd_plan_s* P, int64_t rows) {
     if (e == cudaSuccess)
       e = fdtd::launch_march_f32c(at<fdtd::InstDesc>(P, P->off_desc), at<fdtd::WorkItem>(P, P->off_order), P->nitems,
                                   at<unsigned int>(P, P->off_queue), at<fdtd::SyncWords>(P, P->off_sync),
-                                  P->nclusters, P->csize, smem, s);
+                                  P->grid, s);
     if (e != cudaSuccess) return cuda_fail(P, e, "march_f32c launch");
   }
   for (auto& b : P->inst) b.rows_done = std::min<int64_t>(b.p.nt, b.rows_done + rows);
@@ -397,7 +377,6 @@ fdtd_status batch_march_graph(fdtd_plan_s* P, int64_t rows) {
       P->graph_exec = nullptr;
     }
     cudaStream_t c = P->cap_stream;
-    const size_t smem = fdtd::march_f32c_smem(P->smem_cols);
     e = cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(P, e, "cudaStreamBeginCapture");
     for (int64_t done = 0; done < rows && e == cudaSuccess; done += per) {
@@ -407,7 +386,7 @@ fdtd_status batch_march_graph(fdtd_plan_s* P, int64_t rows) {
       if (e == cudaSuccess)
         e = fdtd::launch_march_f32c(at<fdtd::InstDesc>(P, P->off_desc), at<fdtd::WorkItem>(P, P->off_order),
                                     P->nitems, at<unsigned int>(P, P->off_queue), at<fdtd::SyncWords>(P, P->off_sync),
-                                    P->nclusters, P->csize, smem, c);
+                                    P->grid, c);
     }
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(c, &g);
@@ -463,7 +442,9 @@ fdtd_status batch_readout(fdtd_plan_s* P, int32_t i, int32_t kind, void* dst, in
   const void* src = nullptr;
   switch (kind) {
     case FDTD_READ_ROW:
-      src = P->ws + b.off_ring + sizeof(float2) * (size_t)((b.rows_done - 1) % b.R) * (size_t)b.stride;
+      e = fdtd::launch_row_move(row_map(P, i), b.rows_done - 1, at<float2>(P, P->off_stage), 0, P->stream);
+      if (e != cudaSuccess) return cuda_fail(P, e, "row gather");
+      src = P->ws + P->off_stage;
       break;
     case FDTD_READ_NORMS: src = P->ws + b.off_norms; break;
     case FDTD_READ_SNAPSHOTS: src = P->ws + b.off_snaps; break;

@@ -193,7 +193,7 @@ fdtd_status fdtd_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n_ins
   if (p.init_cond == FDTD_IC_TWO_PHOTON_PAIR && (!(p.alpha2 > 0) || !isfinite(p.k2))) return FDTD_ERR_INVALID_ARG;
   if (p.init_cond == FDTD_IC_TWO_PHOTON_GAUSS && !(p.sigma > 0)) return FDTD_ERR_INVALID_ARG;
   if (p.tstep < -1 || p.rows_per_launch < 0 || p.spin_cycles < 0) return FDTD_ERR_INVALID_ARG;
-  if (p.cluster_ctas < 0 || p.cluster_ctas > 8 || p.mid_weight < 0 || p.mid_weight > 4096) return FDTD_ERR_INVALID_ARG;
+  if (p.cluster_ctas < 0 || p.cluster_ctas > 64 || p.mid_weight < 0 || p.mid_weight > 4096) return FDTD_ERR_INVALID_ARG;
   if (p.max_probes < 0 || p.max_probes > INT32_MAX || p.nt >= INT32_MAX) return FDTD_ERR_INVALID_ARG;
   if (p.precision != FDTD_F64 && p.precision != FDTD_F64_DW) return FDTD_ERR_UNSUPPORTED;
 

@@ -43,9 +43,8 @@ constexpr int kMaxGrid = 1024;       // cap on CTAs of the persistent march
 
 // complex64 compensated march (march_f32c.cu)
 constexpr int kF32Threads = 256;     // threads per CTA
-constexpr int kF32P = 8;             // leading columns of a segment kept in registers
-constexpr int kF32MaxTrunc = 16;     // |c2|^16 < 2^-26 required (|c2| < 0.32)
-constexpr int kClusterMax = 16;      // CTAs per cluster at most
+constexpr int kF32Band = 256;        // rows per band of the complex64 sweep
+constexpr int kGangMax = 64;         // band streams of one complex64 instance at most
 
 // double-float march (march_dw.cu)
 constexpr int kDwThreads = 256;      // threads per CTA; two CTAs per SM
@@ -225,36 +224,43 @@ struct BoundaryArgs {
 struct InstDesc {
   int64_t nx, nt, stride, nphi;
   int64_t range[2];        // rows [range[0], range[1]) marched by the current launch; range[1] = rows done
-  int64_t smem_cols;       // pair-sum columns per CTA that fit the launch's shared memory
-  int D, R, kfix, khalo, mid_weight, tstep;
+  int D, R, tstep, pad0;
+  long long spin;          // clock cycles a bounded wait spins before latching FDTD_ERR_TIMEOUT
   float2 d1, c2, c3, gs;   // c1 - 1, c2, c3, -(Gamma/4)/A
   float2 d1lo, c2lo, c3lo; // their FP32 rounding errors: d1 = d1 + d1lo to ~2^-48 (a coefficient
                            // error is the same at every step, so it would grow linearly along
                            // a characteristic)
-  float2 c2pow[kF32MaxTrunc + 1];
-  float2 c2powlo[kF32MaxTrunc + 1];
+  float2 pad1;
   double C, delta;
-  float2* ring;            // R rows x stride complex64
+  float2* ring;            // inner columns j < D: R rows x stride complex64, row-major
+  float2* skew;            // columns j >= D: element (n, j) at skew[((n + j - D) mod rd) R + n mod R]
+                           // (a warp's 32 rows at one sweep step are 32 consecutive entries)
+  int64_t rd;              // nx - D
   float2* snaps;           // or null
-  float2* lo;              // 2 x lo_pitch: TwoSum remainders by consumer column, two row slots
-  int64_t lo_pitch;        // >= nx + 4, a multiple of 8 elements (slots 64-byte aligned)
-  double* partials;        // 2 x kClusterMax
+  float2* lo_in;           // 2 x dpad: TwoSum remainders of the inner columns (j < D), by row parity
+  float2* lo_row;          // nx: remainders of columns j >= D of the last row of the latest band
+  float2* lo_edge;         // nt: remainder of column D-1 of every row
+  int64_t dpad;            // >= D, a multiple of 8 elements
+  unsigned long long* bsync;  // [0] rows whose inner columns are complete; [1 + r] progress of
+                              // band stream r: (first row of its band << 32) + columns of the
+                              // band's last row done
   double* norms;           // nt
   const cd* etab;          // FP64 tables
   const cd* phitab;
   const float2* etab32;    // FP32 copies
-  const float2* phitab32;
-  const float2* detab32;
+  const float2* phitab32;  // [-1] and the entries after the table's end are 0
+  const float2* detab32;   // [-1] and the entries after the table's end are 0
   const float2* rowscal32;
   const float2* bnd32;     // 2 per row: psi(-a, n delta) as FP32 hi and lo
   const double* bnorm;     // per row: (1/2)|psi(-a, n delta)|^2
 };
 
-// one entry of the batched march's queue
+// one entry of the batched march's queue: band stream `stream` of `g` of one instance
 struct WorkItem {
-  int count;               // instances in the item
-  int solo;                // 1: one instance per CTA; 0: inst[0] over the whole cluster
-  int inst[kClusterMax];
+  int inst;
+  int stream;
+  int g;
+  int pad;
 };
 
 }  // namespace fdtd
@@ -263,9 +269,10 @@ struct WorkItem {
 struct fdtd_batch_inst {
   fdtd_params p;
   size_t off_etab, off_phi, off_rowscal, off_detab, off_norms, off_hscr, off_etab32, off_phi32, off_rowscal32,
-      off_detab32, off_ring, off_snaps, off_lo, off_part, off_bnd, off_bnorm;
-  int64_t stride, nphi, nsnap, cols_max;
-  int R, kfix, khalo;
+      off_detab32, off_ring, off_skew, off_snaps, off_lo, off_bsync, off_bnd, off_bnorm;
+  int64_t stride, nphi, nsnap;
+  int64_t dpad, nxpad, lo_elems;  // remainders: lo_in 2 x dpad, lo_row nxpad, lo_edge nt
+  int R, g;                       // ring rows; CTAs that march the instance together
   fdtd::cd c1, c2, c3, cs, gs;
   double C;
   int64_t rows_done;
@@ -308,10 +315,9 @@ struct fdtd_plan_s {
   // complex64 (batched) plans
   bool batched = false;
   std::vector<fdtd_batch_inst> inst;
-  size_t off_desc = 0, off_order = 0, off_queue = 0, off_eargs = 0;
+  size_t off_desc = 0, off_order = 0, off_queue = 0, off_eargs = 0, off_stage = 0;
   int nitems = 0;
-  int csize = 0, nclusters = 0;
-  int64_t smem_cols = 0;
+  int gang_max = 0;          // band streams of one instance at most
   // fdtd_march_graph: the recorded launch sequence of one march length
   cudaGraphExec_t graph_exec = nullptr;
   int64_t graph_rows = -1;
@@ -379,10 +385,23 @@ cudaError_t launch_measures(const cd* snaps, int64_t nx, int tstep, int64_t nsna
 cudaError_t launch_march_f64(const MarchArgs& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_tables32(const InstDesc& I, const cd* detab, const cd* rowscal, cudaStream_t s);
 cudaError_t launch_advance(InstDesc* insts, int ninst, int64_t rows, cudaStream_t s);
-size_t march_f32c_smem(int64_t cols);
-int march_f32c_max_clusters(int csize, size_t smem);
+// where row r of a complex64 instance lives (inner ring and anti-diagonal ring)
+struct RowMap {
+  float2* ring;
+  int64_t stride;
+  float2* skew;
+  int64_t rd, nx;
+  int R, D;
+};
+// row r between the rings and a row-major buffer: dir 0 gathers into buf, 1 scatters
+// buf into the rings, 2 writes zeros into the rings
+cudaError_t launch_row_move(const RowMap& m, int64_t r, float2* buf, int dir, cudaStream_t s);
+int march_f32c_blocks_per_sm();
+}  // namespace fdtd
+fdtd::RowMap row_map(fdtd_plan_s* P, int i);  // instance i of a complex64 plan (batch_api.cu)
+namespace fdtd {
 cudaError_t launch_march_f32c(const InstDesc* insts, const WorkItem* items, int nitems, unsigned int* queue,
-                              SyncWords* sync, int nclusters, int csize, size_t smem, cudaStream_t s);
+                              SyncWords* sync, int grid, cudaStream_t s);
 int march_f64_max_grid(int device);
 int march_dw_max_grid(int device);
 cudaError_t launch_tables_dw(const cd* etab, const cd* phitab, const cd* rowscal, const cd* detab, double C,

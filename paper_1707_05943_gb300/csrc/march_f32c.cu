@@ -8,28 +8,61 @@
 // and is formed in FP32.  The only term with weight ~1 is a, which is carried
 // along its characteristic as an unevaluated pair a_hi + a_lo: a_hi is the
 // complex64 value in the ring, a_lo the rounding error of the sum that
-// produced it, recovered exactly by TwoSum(a_hi, S) (Knuth) and kept on chip
-// (a two-slot array by row parity, L2-resident) until the next row consumes it
-// at column m+1.  The boundary tables, the exact boundary value
+// produced it, recovered exactly by TwoSum(a_hi, S) (Knuth) and handed to the
+// update of column m+1 of the next row.  The coefficients carry FP32 low parts
+// (a coefficient error is the same at every step, so it would grow linearly
+// along a characteristic).  The boundary tables, the exact boundary value
 // psi(-a, t) at the first column and the norm reduction stay FP64.
 //
-// Work layout: thread-block clusters of up to 8 CTAs x 256 threads.  A
-// cluster takes the next work item from a queue (largest first): either one
-// wide instance, whose columns it splits over its CTAs (the costlier region
-// -a < x <= 3a on CTAs of its own when it is worth one, see cta_range) and
-// whose rows it marches with one cluster barrier per row, or up to one narrow
-// instance per CTA, marched with CTA barriers only.
-// Either way rows n-1, n-D and n-D-1 are complete when row n starts.  Inside a CTA each thread owns a contiguous
-// segment and runs the recurrence y_m = c2 y_{m-1} + r_m over it from a zero
-// carry; after a CTA barrier it takes its carry from the threads before it
-// and corrects its first kfix columns (|c2|^kfix < 2^-26, below FP32
-// rounding).  Clusters never wait on each other: the queue counter is the only
-// state they share, so the launch needs no co-residency.
+// Work layout: bands of 256 consecutive rows, one row per thread.
+//  * Inner columns -a < x <= a (storage columns j < D): the mirror term of
+//    Eq. 1 reads row n-j-1 at column D-j-1, to the RIGHT of j, so these columns
+//    go row by row: each thread takes a few columns, forms their sources, and
+//    an exact affine scan over the threads (y -> c2^L y + Y per segment) gives
+//    every segment its carry of the row recurrence y_m = c2 y_{m-1} + r_m.
+//  * Columns x > a (j >= D): every read lies to the left or D rows back, so the
+//    band sweeps them left to right as a systolic array: lane l of warp w marches
+//    row n0 + 32w + l one column per step, one column behind the lane above.
+//    Row n-1's value, its TwoSum remainder and its delay pair sum reach the lane
+//    from the lane above by warp shuffles; lane 0 takes them from the warp above
+//    through a shared-memory queue, warp 0 from the previous band's last row in
+//    global memory.  The recurrence along the row is the lane's own running
+//    value: exact, with no carries and no barriers.  Each lane streams one new
+//    delay value (row n-D) per step, prefetched two steps ahead.
+// A band is one CTA.  Every CTA of the persistent (cooperative) launch takes band
+// streams from a queue, largest instance first: an instance with gang size g
+// (set on the host from its share of the work) is split into g streams, stream r
+// marching bands r, r + g, r + 2g, ...; so up to g bands (256 g rows) of one
+// instance are in flight.  Band c waits (bounded) for band c-1's inner columns
+// before its own, and its warp 0 for band c-1's last row before each chunk of 32
+// columns; a ring of D + 2 + 256 g + 32 rows keeps every row an in-flight band
+// reads.  The results do not depend on how rows fall into bands: every value is
+// formed by the same operations in the same order whichever band, warp or lane
+// computes it.
 #include <cuda_runtime.h>
 
 #include "fdtd_internal.cuh"
 
 namespace fdtd {
+
+namespace {
+
+constexpr int kBand = kF32Band;           // rows per band: one per thread
+constexpr int kWarps = kF32Threads / 32;  // warps per band
+constexpr int kHandQ = 64;                // queue entries between consecutive warps (power of two)
+constexpr int kGrp = 8;                   // sweep steps between queue bookkeeping
+constexpr int kChunk = 32;                // columns of the previous band's last row staged at a time
+constexpr int kPre = 2;                   // prefetch distance (sweep steps) of a lane's streams
+constexpr int kInnerPer = 8;              // inner columns per thread and pass (2048 per pass)
+static_assert(kBand == kF32Threads, "one row per thread");
+static_assert(kPre == 2 && kGrp % kPre == 0 && kChunk % kGrp == 0, "sweep step grouping");
+static_assert(kHandQ >= 31 + 2 * kGrp + 16, "queue too short for the sweep's lag");
+
+struct Hand {
+  float2 hi, lo, hn;  // psi[n][j] (hi, TwoSum remainder) and the delay pair sum of row n-D
+};
+
+}  // namespace
 
 __device__ __forceinline__ float2 f2(float r, float i) { return make_float2(r, i); }
 __device__ __forceinline__ float2 add(float2 a, float2 b) { return f2(a.x + b.x, a.y + b.y); }
@@ -43,6 +76,17 @@ __device__ __forceinline__ float2 fmac(float2 a, float2 b, float2 acc) {  // acc
   return acc;
 }
 __device__ __forceinline__ float2 scal(float s, float2 a) { return f2(s * a.x, s * a.y); }
+__device__ __forceinline__ float2 shfl_up2(float2 v, int d) {
+  return f2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+}
+
+// 8-byte asynchronous copies global -> shared (completion by commit groups)
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // TwoSum: s = fl(a+b), e = (a+b) - s exactly (round to nearest, no FMA involved)
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -51,596 +95,618 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-__device__ __forceinline__ float2 ldr(const float2* p) { return *p; }
-
+// psi at x <= -a (c <= -D/2): C phi(-a - (r - c - D/2) delta) e(r delta) from the FP32 tables
 __device__ __forceinline__ float2 psi_left32(const InstDesc& I, int64_t r, int64_t c) {
   const int Dh = I.D >> 1;
   return scal((float)I.C, mulc(I.phitab32[r - c - Dh], I.etab32[r]));
 }
 
-__device__ __forceinline__ float2 psi_any32(const InstDesc& I, int64_t n, int nslot, int64_t r, int64_t c) {
-  const int Dh = I.D >> 1;
-  if (c <= -Dh) return psi_left32(I, r, c);
-  int slot = nslot - (int)(n - r);
-  if (slot < 0) slot += I.R;
-  return ldr(&I.ring[(int64_t)slot * I.stride + (c + Dh - 1)]);
-}
-
-struct RowF {
-  int64_t n;
-  int nslot;
-  const float2* row1;
-  const float2* rowD;
-  const float2* rowD1;
-  float2 R1, R2;
-  float2* hs;
-  int64_t hbase;
-  bool cold;
-};
-
-// S without the a_lo and c2 y_{m-1} parts, and a_hi, for a column of -a < x <= 3a.
-// Its up to 14 reads (stencil, delay square, the mirror bars of lines 2-3) go
-// to scattered rows; they are all issued before any is used.
-__device__ __noinline__ float2 rhs_general32(const InstDesc& I, int64_t n, int nslot, int64_t j, float2 R2,
-                                             float2* a_hi) {
-  const int D = I.D, Dh = D >> 1;
+// S without a_lo and the c2 y term, and a_hi, for an inner column 0 <= j < D of row n
+// (m = j - D/2 + 1 <= D/2).  The delay square lies at x <= -a; the mirror bar of row
+// r2 = n - j - 1 reads columns D-j-2, D-j-1 of the ring.
+__device__ __forceinline__ float2 rhs_inner32(const InstDesc& I, int64_t n, int nslot, int64_t j, float2 R2,
+                                              float2* a_hi) {
+  const int D = I.D, Dh = D >> 1, R = I.R;
   const int64_t m = j - Dh + 1;
-  const int64_t r2 = n - m - Dh, r3 = n - m + Dh;
-  const bool dl = (n >= D + 1), s2 = (r2 >= 0), s3 = (m >= Dh + 1) && (r3 >= 0);
-  int64_t rr[14], cc[14];
-  bool ok[14];
-  rr[0] = n - 1; cc[0] = m - 1; ok[0] = true;
-  rr[1] = n - 1; cc[1] = m; ok[1] = true;
-  rr[2] = n - D; cc[2] = m - D; rr[3] = n - D; cc[3] = m - D - 1;
-  rr[4] = n - D - 1; cc[4] = m - D; rr[5] = n - D - 1; cc[5] = m - D - 1;
-  ok[2] = ok[3] = ok[4] = ok[5] = dl;
-  rr[6] = r2; cc[6] = -m - D; rr[7] = r2; cc[7] = -m - D + 1; rr[8] = r2; cc[8] = -m; rr[9] = r2; cc[9] = -m + 1;
-  ok[6] = ok[7] = ok[8] = ok[9] = s2;
-  rr[10] = r3; cc[10] = D - m; rr[11] = r3; cc[11] = D - m + 1; rr[12] = r3; cc[12] = -m; rr[13] = r3; cc[13] = -m + 1;
-  ok[10] = ok[11] = ok[12] = ok[13] = s3;
-  // unconditional loads (indices clamped into the tables and the ring), selected below
-  float2 ph[14], ev[14], rg[14];
-#pragma unroll
-  for (int k = 0; k < 14; ++k) {
-    int64_t ai = rr[k] - cc[k] - Dh;
-    ai = ai < 0 ? 0 : (ai >= I.nphi ? I.nphi - 1 : ai);
-    int64_t ei = rr[k] < 0 ? 0 : (rr[k] >= I.nt ? I.nt - 1 : rr[k]);
-    int lag = (int)(n - rr[k]);
-    lag = lag < 0 ? 0 : (lag >= I.R ? I.R - 1 : lag);
-    int slot = nslot - lag;
-    if (slot < 0) slot += I.R;
-    int64_t ci = cc[k] + Dh - 1;
-    ci = ci < 0 ? 0 : (ci >= I.nx ? I.nx - 1 : ci);
-    ph[k] = I.phitab32[ai];
-    ev[k] = I.etab32[ei];
-    rg[k] = ldr(&I.ring[(int64_t)slot * I.stride + ci]);
-  }
-  const float2 chi = I.phitab32[s2 ? r2 : 0];
-  float2 v[14];
-#pragma unroll
-  for (int k = 0; k < 14; ++k)
-    v[k] = !ok[k] ? f2(0.f, 0.f) : ((cc[k] <= -Dh) ? scal((float)I.C, mulc(ph[k], ev[k])) : rg[k]);
-  *a_hi = v[0];
-  float2 S = mulc(I.d1, v[0]);
-  S = fmac(I.c2, v[1], S);
-  float2 L = mulc(I.d1lo, v[0]);  // the coefficients' low parts
-  L = fmac(I.c2lo, v[1], L);
+  int s1 = nslot - 1;
+  if (s1 < 0) s1 += R;
+  const float2* row1 = I.ring + (int64_t)s1 * I.stride;
+  const float2 v0 = (j >= 1) ? row1[j - 1] : psi_left32(I, n - 1, m - 1);
+  const float2 v1 = row1[j];
+  const bool dl = (n >= D + 1);
+  const int64_t r2 = n - j - 1;
+  const bool s2 = (r2 >= 0);
+  float2 v2 = f2(0.f, 0.f), v3 = v2, v4 = v2, v5 = v2, v6 = v2, v7 = v2, v8 = v2, v9 = v2, chi = v2;
   if (dl) {
-    const float2 sq = add(add(v[2], v[3]), add(v[4], v[5]));
+    v2 = psi_left32(I, n - D, m - D);
+    v3 = psi_left32(I, n - D, m - D - 1);
+    v4 = psi_left32(I, n - D - 1, m - D);
+    v5 = psi_left32(I, n - D - 1, m - D - 1);
+  }
+  if (s2) {
+    int s = nslot - (int)(j + 1);
+    if (s < 0) s += R;
+    const float2* rowr = I.ring + (int64_t)s * I.stride;
+    v6 = psi_left32(I, r2, -m - D);
+    v7 = psi_left32(I, r2, -m - D + 1);
+    v8 = (j < D - 1) ? rowr[D - 2 - j] : psi_left32(I, r2, -m);
+    v9 = rowr[D - 1 - j];
+    chi = I.phitab32[r2];
+  }
+  *a_hi = v0;
+  float2 S = mulc(I.d1, v0);
+  S = fmac(I.c2, v1, S);
+  float2 L = mulc(I.d1lo, v0);
+  L = fmac(I.c2lo, v1, L);
+  if (dl) {
+    const float2 sq = add(add(v2, v3), add(v4, v5));
     S = fmac(I.c3, sq, S);
     L = fmac(I.c3lo, sq, L);
   }
   S = add(S, L);
   if (s2) {
     const float w = (r2 == 0) ? 0.5f : 1.0f;
-    S = fmac(I.gs, scal(w, sub(add(v[6], v[7]), add(v[8], v[9]))), S);
+    S = fmac(I.gs, scal(w, sub(add(v6, v7), add(v8, v9))), S);
     S = fmac(R2, chi, S);
   }
-  if (s3) {
+  return S;
+}
+
+// the mirror terms of a column D <= j < 2D (a < x <= 3a) of row n, added to S: the
+// bar of row r2 = n-j-1 lies at x <= -a; the bar of row r3 = r2 + D reads ring
+// columns 2D-j-2, 2D-j-1 (inner columns) and the boundary tables
+__device__ __noinline__ float2 general_extra32(const InstDesc& I, int n, int nslot, int j, float2 R2, float2 S) {
+  const int D = I.D, Dh = D >> 1;
+  const int m = j - Dh + 1;
+  const int r2 = n - j - 1, r3 = r2 + D;
+  if (r2 >= 0) {
+    const float2 v6 = psi_left32(I, r2, -m - D), v7 = psi_left32(I, r2, -m - D + 1);
+    const float2 v8 = psi_left32(I, r2, -m), v9 = psi_left32(I, r2, -m + 1);
+    const float w = (r2 == 0) ? 0.5f : 1.0f;
+    S = fmac(I.gs, scal(w, sub(add(v6, v7), add(v8, v9))), S);
+    S = fmac(R2, I.phitab32[r2], S);
+  }
+  if (r3 >= 0) {
+    int s = nslot - (j + 1 - D);
+    if (s < 0) s += I.R;
+    const float2* rowr = I.ring + (int64_t)s * I.stride;
+    const float2 v10 = (j <= 2 * D - 2) ? rowr[2 * D - 2 - j] : psi_left32(I, r3, D - m);
+    const float2 v11 = rowr[2 * D - 1 - j];
+    const float2 v12 = psi_left32(I, r3, -m), v13 = psi_left32(I, r3, -m + 1);
     const float w = (r3 == 0) ? 0.5f : 1.0f;
-    S = fmac(I.gs, scal(w, sub(add(v[10], v[11]), add(v[12], v[13]))), S);
+    S = fmac(I.gs, scal(w, sub(add(v10, v11), add(v12, v13))), S);
   }
   return S;
 }
 
-__device__ __forceinline__ float2 rhs_bulk32(const InstDesc& I, const RowF& R, int64_t j, float2* a_hi) {
-  const int D = I.D;
-  float2 a = ldr(R.row1 + j - 1);
-  *a_hi = a;
-  const float2 b = ldr(R.row1 + j);
-  float2 S = mulc(I.d1, a);
-  S = fmac(I.c2, b, S);
-  float2 L = fmac(I.c2lo, b, mulc(I.d1lo, a));
-  if (R.rowD) {
-    float2 hn = add(ldr(R.rowD + j - D - 1), ldr(R.rowD + j - D));
-    if (R.rowD1) {
-      float2 hp = (R.hs && !R.cold) ? R.hs[j - R.hbase] : add(ldr(R.rowD1 + j - D - 1), ldr(R.rowD1 + j - D));
-      const float2 sq = add(hn, hp);
-      S = fmac(I.c3, sq, S);
-      L = fmac(I.c3lo, sq, L);
+__device__ __forceinline__ void latch_timeout(SyncWords* sync, int64_t n) {
+  if (atomicCAS(&sync->status, 0u, (unsigned)FDTD_ERR_TIMEOUT) == 0u) sync->where = n;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];\n" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+// bounded waits: poll until *p >= target, giving up after `spin` cycles (latching
+// FDTD_ERR_TIMEOUT) or as soon as an error is latched; the polls are relaxed, the
+// final read an acquire (GPU scope) or a CTA fence (shared memory)
+__device__ __noinline__ void wait_ge_global_slow(const unsigned long long* p, unsigned long long target,
+                                                 long long spin, SyncWords* sync, int64_t n) {
+  const long long t0 = clock64();
+  for (int k = 1;; ++k) {
+    __nanosleep(64);
+    if (ld_relaxed_u64(p) >= target) return;
+    if ((k & 15) == 0 && *(volatile unsigned int*)&sync->status != 0u) return;
+    if (clock64() - t0 > spin) {
+      latch_timeout(sync, n);
+      return;
     }
-    if (R.hs) R.hs[j - R.hbase] = hn;
   }
+}
+__device__ __forceinline__ void wait_ge_global(const unsigned long long* p, unsigned long long target, long long spin,
+                                               SyncWords* sync, int64_t n) {
+  if (ld_relaxed_u64(p) < target) wait_ge_global_slow(p, target, spin, sync, n);
+  (void)ld_acquire_u64(p);
+}
+__device__ __noinline__ void wait_ge_shared_slow(volatile int* p, int target, long long spin, SyncWords* sync,
+                                                 int64_t n) {
+  const long long t0 = clock64();
+  for (int k = 1;; ++k) {
+    __nanosleep(32);
+    if (*p >= target) return;
+    if ((k & 63) == 0 && *(volatile unsigned int*)&sync->status != 0u) return;
+    if (clock64() - t0 > spin) {
+      latch_timeout(sync, n);
+      return;
+    }
+  }
+}
+__device__ __forceinline__ void wait_ge_shared(volatile int* p, int target, long long spin, SyncWords* sync,
+                                               int64_t n) {
+  if (*p < target) wait_ge_shared_slow(p, target, spin, sync, n);
+  __threadfence_block();
+}
+
+// ---------------------------------------------------------------- inner columns
+// rows n0 .. n0+h-1, columns 0 .. D-1, row by row (every thread of the CTA)
+__device__ __noinline__ void inner_rows(const InstDesc& I, int64_t n0, int h, float (*s_wn)[kBand],
+                                           float2* s_scP, float2* s_scY, float2* s_ylast) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int D = I.D;
+  for (int r = 0; r < h; ++r) {
+    const int64_t n = n0 + r;
+    const int nslot = (int)(n % I.R);
+    float2* row0 = I.ring + (int64_t)nslot * I.stride;
+    const float2* lo_rd = I.lo_in + (int64_t)((n - 1) & 1) * I.dpad;
+    float2* lo_wr = I.lo_in + (int64_t)(n & 1) * I.dpad;
+    const float2 R2 = I.rowscal32[2 * n + 1];
+    float2* snap = (I.tstep >= 0 && n % (I.tstep + 1) == 0) ? I.snaps + (n / (I.tstep + 1)) * I.nx : nullptr;
+    float2 ycar = I.bnd32[2 * n];  // psi(-a, n delta): the value left of column 0
+    float nacc = 0.f;
+    for (int c0 = 0; c0 < D; c0 += kBand * kInnerPer) {
+      const int cw = (D - c0 < kBand * kInnerPer) ? D - c0 : kBand * kInnerPer;
+      const int L = (cw + kBand - 1) / kBand;
+      const int j0 = c0 + tid * L;
+      const int j1 = (j0 + L < c0 + cw) ? j0 + L : c0 + cw;
+      // sources of the thread's columns, and its segment as an affine map y -> P y + Y
+      float2 rv[kInnerPer], av[kInnerPer];
+      float2 P = f2(1.f, 0.f), Y = f2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < kInnerPer; ++u) {
+        rv[u] = av[u] = f2(0.f, 0.f);
+        if (j0 + u < j1) {
+          const int j = j0 + u;
+          float2 ah, al;
+          float2 S = rhs_inner32(I, n, nslot, j, R2, &ah);
+          if (j == 0) {  // a = psi(-a, (n-1) delta), exact as hi + lo
+            ah = I.bnd32[2 * (n - 1)];
+            al = I.bnd32[2 * (n - 1) + 1];
+          } else {
+            al = lo_rd[j - 1];
+          }
+          S = add(S, al);
+          rv[u] = S;
+          av[u] = ah;
+          Y = add(ah, fmac(I.c2lo, Y, fmac(I.c2, Y, S)));
+          P = mulc(P, I.c2);
+        }
+      }
+      // inclusive scan of the maps over the lanes: (earlier) then (later) =
+      // (P_e P_l, P_l Y_e + Y_l)
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const float2 Pp = shfl_up2(P, off), Yp = shfl_up2(Y, off);
+        if (lane >= off) {
+          Y = fmac(Yp, P, Y);
+          P = mulc(Pp, P);
+        }
+      }
+      if (lane == 31) {
+        s_scP[warp] = P;
+        s_scY[warp] = Y;
+      }
+      float2 Pe = shfl_up2(P, 1), Ye = shfl_up2(Y, 1);
+      if (lane == 0) {
+        Pe = f2(1.f, 0.f);
+        Ye = f2(0.f, 0.f);
+      }
+      __syncthreads();
+      float2 Pw = f2(1.f, 0.f), Yw = f2(0.f, 0.f);
+      for (int q = 0; q < warp; ++q) {
+        const float2 Pq = s_scP[q], Yq = s_scY[q];
+        Yw = fmac(Yw, Pq, Yq);
+        Pw = mulc(Pw, Pq);
+      }
+      // the carry into the segment: the maps of every earlier segment applied to ycar
+      float2 y = fmac(mulc(Pw, Pe), ycar, fmac(Yw, Pe, Ye));
+#pragma unroll
+      for (int u = 0; u < kInnerPer; ++u) {
+        if (j0 + u < j1) {
+          const int j = j0 + u;
+          const float2 S = fmac(I.c2lo, y, fmac(I.c2, y, rv[u]));
+          float2 sv, e;
+          two_sum(av[u].x, S.x, sv.x, e.x);
+          two_sum(av[u].y, S.y, sv.y, e.y);
+          row0[j] = sv;
+          lo_wr[j] = e;
+          if (j == D - 1) I.lo_edge[n] = e;
+          if (snap) snap[j] = sv;
+          const float wt = (j == I.nx - 1) ? 0.5f : 1.0f;
+          nacc = fmaf(wt * sv.x, sv.x, nacc);
+          nacc = fmaf(wt * sv.y, sv.y, nacc);
+          y = sv;
+        }
+      }
+      if (j0 < j1 && j1 == c0 + cw) *s_ylast = y;  // carry into the next pass
+      __syncthreads();  // row n's inner columns are stored; the scan buffers are free
+      ycar = *s_ylast;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nacc += __shfl_down_sync(0xffffffffu, nacc, o);
+    if (lane == 0) s_wn[warp][r] = nacc;
+  }
+}
+
+// ---------------------------------------------------------------- sweep of x > a
+// Lane l of a warp marches row n = nw + l (nw: the warp's first row) one column per
+// step, one column behind lane l-1: at step k it takes column j = D + q, q = k - l.
+// The warp's 32 rows at step k then share the anti-diagonal d = n + q = nw + k, so
+// its stores and its reads of the delay row n-D (d - 2D) are 32 consecutive entries
+// of the skew ring.
+
+// a lane's prefetched operands of one step: the delay value (row n-D, column q) and
+// the source tables at i = n-1-q
+struct Pre {
+  float2 d, e, f;
+};
+
+// the constants of one lane's sweep
+struct SweepC {
+  const InstDesc* I;
+  float2* skew;
+  const float2* rowD_in;   // inner ring row n-D (columns < D)
+  const float2* __restrict__ detab32;
+  const float2* __restrict__ phitab32;
+  float2* lo_row;
+  float2* snap;
+  Hand* hand_out;          // queue to the warp below (lane 31), or null
+  int R, n, nslot, sD, lane, D, nx, ncols, rd;
+  bool row_on, useD, is_last;
+  float2 R1, R2, d1, c2, c3, d1l, c2l, c3l;  // c3, c3l: 0 for rows without the delay square (n <= D)
+};
+
+// its running state
+struct SweepS {
+  float2 y, a_hi, a_lo, o_hi, o_lo, o_hn, dprev;
+  float nacc;
+  double dacc;
+  int dout;  // d-row (mod rd) of this step's outputs
+  int dpre;  // d-row (mod rd) of the delay value kPre steps ahead
+  Pre pq[kPre];
+};
+
+__device__ __forceinline__ Pre sweep_fetch(const SweepC& c, int k, int dpre) {
+  const int q = k - c.lane;
+  Pre v;
+  const float2 z = f2(0.f, 0.f);
+  if (!c.useD) v.d = z;
+  else if (q >= c.D) v.d = c.skew[(int64_t)dpre * c.R + c.sD];
+  else v.d = (q >= 0) ? c.rowD_in[q] : z;
+  // i < 0 (outside the light cone) and i - D < 0 read the tables' zero entry at -1
+  const int i = c.n - 1 - q, ip = i - c.D;
+  v.e = c.detab32[i < -1 ? -1 : i];
+  v.f = c.phitab32[ip < -1 ? -1 : ip];
+  return v;
+}
+
+// one step.  FAST: every lane of the warp is marching a column of x > 3a (j >= 2D)
+// other than the last one
+template <bool FAST, int QI>
+__device__ __forceinline__ void sweep_step(const SweepC& c, SweepS& st, int k, float2 b_hi, float2 b_lo, float2 hp) {
+  const int q = k - c.lane;
+  const bool act = FAST || (c.row_on && (unsigned)q < (unsigned)c.ncols);
+  const int j = c.D + q;
+  const Pre pv = st.pq[QI];
+  const float2 hn = add(st.dprev, pv.d);
+  float2 S = mulc(c.d1, st.a_hi);
+  S = fmac(c.c2, b_hi, S);
+  float2 L = fmac(c.c2l, b_hi, mulc(c.d1l, st.a_hi));
+  const float2 sq = add(hn, hp);
+  S = fmac(c.c3, sq, S);
+  L = fmac(c.c3l, sq, L);
   S = add(S, L);
-  const int64_t i = R.n - j - 1 + D;  // r2 + D
-  if (i >= 0) {
-    S = fmac(R.R1, I.detab32[i], S);
-    if (i >= D) S = fmac(R.R2, I.phitab32[i - D], S);
+  if (FAST || j >= 2 * c.D) {
+    S = fmac(c.R1, pv.e, S);
+    S = fmac(c.R2, pv.f, S);
+  } else if (act) {
+    S = general_extra32(*c.I, c.n, c.nslot, j, c.R2, S);
   }
-  return S;
-}
-
-__device__ __forceinline__ float2 rhs32(const InstDesc& I, const RowF& R, int64_t j, float2* a_hi) {
-  if (j >= 2 * (int64_t)I.D) return rhs_bulk32(I, R, j, a_hi);
-  return rhs_general32(I, R.n, R.nslot, j, R.R2, a_hi);
-}
-
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
-  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-}
-__device__ __forceinline__ unsigned cluster_rank() {
-  unsigned r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ unsigned cluster_size() {
-  unsigned r;
-  asm volatile("mov.u32 %0, %%cluster_nctarank;\n" : "=r"(r));
-  return r;
-}
-// read a 32-bit word from CTA `rank`'s shared memory (same offset)
-__device__ __forceinline__ int ld_dsmem_i32(const int* local, unsigned rank) {
-  unsigned a = (unsigned)__cvta_generic_to_shared(local), ra;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(ra) : "r"(a), "r"(rank));
-  int v;
-  asm volatile("ld.shared::cluster.s32 %0, [%1];\n" : "=r"(v) : "r"(ra) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ float ld_dsmem_f32(const float* local, unsigned rank) {
-  unsigned a = (unsigned)__cvta_generic_to_shared(local), ra;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(ra) : "r"(a), "r"(rank));
-  float v;
-  asm volatile("ld.shared::cluster.f32 %0, [%1];\n" : "=f"(v) : "r"(ra) : "memory");
-  return v;
-}
-
-// columns of CTA `rank` of `C` for an instance.  The first G2 = 2D columns
-// (-a < x <= 3a) cost mid_weight bulk columns each.  When they are worth about
-// one CTA or more, whole CTAs take them (split evenly) and the others the bulk
-// (split evenly), so that no CTA mixes the two kinds; otherwise one cost-weighted
-// split.  The host mirrors this rule to size shared memory.
-__device__ __forceinline__ void cta_range(const InstDesc& I, int rank, int C, int64_t* lo, int64_t* hi) {
-  const int64_t G2 = (2 * (int64_t)I.D < I.nx) ? 2 * (int64_t)I.D : I.nx;
-  const int64_t wm = I.mid_weight;
-  const int64_t W = wm * G2 + (I.nx - G2);
-  int64_t g = (2 * (int64_t)C * wm * G2 + W) / (2 * W);
-  if (g > C - 1) g = C - 1;
-  if (g >= 1 && I.nx > G2) {
-    if (rank < g) {
-      *lo = G2 * rank / g;
-      *hi = G2 * (rank + 1) / g;
+  S = add(S, st.a_lo);
+  S = fmac(c.c2l, st.y, fmac(c.c2, st.y, S));
+  float2 sv, e;
+  two_sum(st.a_hi.x, S.x, sv.x, e.x);
+  two_sum(st.a_hi.y, S.y, sv.y, e.y);
+  if (act) {
+    c.skew[(int64_t)st.dout * c.R + c.nslot] = sv;
+    if (c.snap) c.snap[j] = sv;
+    if (c.is_last) c.lo_row[j] = e;
+    if (c.hand_out) c.hand_out[q & (kHandQ - 1)] = Hand{sv, e, hn};
+    if (FAST) {
+      st.nacc = fmaf(sv.x, sv.x, st.nacc);
+      st.nacc = fmaf(sv.y, sv.y, st.nacc);
     } else {
-      const int64_t r = rank - g, Cb = C - g;
-      *lo = G2 + (I.nx - G2) * r / Cb;
-      *hi = G2 + (I.nx - G2) * (r + 1) / Cb;
+      const float wt = (j == c.nx - 1) ? 0.5f : 1.0f;
+      st.nacc = fmaf(wt * sv.x, sv.x, st.nacc);
+      st.nacc = fmaf(wt * sv.y, sv.y, st.nacc);
+    }
+    if ((q & 15) == 15) {  // FP32 sums of 16 columns, FP64 across them
+      st.dacc += (double)st.nacc;
+      st.nacc = 0.f;
+    }
+    st.o_hi = sv;
+    st.o_lo = e;
+    st.o_hn = hn;
+    st.y = sv;
+    st.a_hi = b_hi;
+    st.a_lo = b_lo;
+    st.dprev = pv.d;
+  }
+  if (c.D < 32) __syncwarp();  // a lane may read the row of a lane D below soon
+  st.dout = (st.dout + 1 == c.rd) ? 0 : st.dout + 1;
+  st.pq[QI] = sweep_fetch(c, k + kPre, st.dpre);
+  st.dpre = (st.dpre + 1 == c.rd) ? 0 : st.dpre + 1;
+}
+
+// the ring entry of row r (>= 0), column col (0 <= col < nx)
+__device__ __forceinline__ const float2* ring_at(const InstDesc& I, int r, int col) {
+  if (col < I.D) return I.ring + (int64_t)(r % I.R) * I.stride + col;
+  return I.skew + (int64_t)((r + col - I.D) % (int)I.rd) * I.R + (r % I.R);
+}
+
+// rows n0 .. n0+h-1 (row n0+tid on thread tid), columns D .. nx-1.  wait_prev:
+// band c-1 (progress word prev_word, first row n0-256) is still being marched.
+__device__ __noinline__ void sweep(const InstDesc& I, int n0, int h, bool wait_prev,
+                                   const unsigned long long* prev_word, unsigned long long* my_word,
+                                   SyncWords* sync, Hand (*s_hand)[kHandQ], volatile int* s_prod,
+                                   volatile int* s_cons, float2 (*s_pv_hi)[kChunk], float2 (*s_pv_lo)[kChunk],
+                                   float2 (*s_pv_d)[kChunk + 1], const float (*s_wn)[kBand]) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (warp * 32 >= h) return;
+  const float2 z = f2(0.f, 0.f);
+  const int D = I.D, Dh = D >> 1, R = I.R;
+  const int nx = (int)I.nx, ncols = nx - D;
+  const long long spin = I.spin;
+  const bool row_on = tid < h;
+  const int n = n0 + (row_on ? tid : 0);
+  const int nw = n0 + 32 * warp;
+  const bool next_on = (warp + 1 < kWarps) && ((warp + 1) * 32 < h);
+  const bool warp_full = (warp + 1) * 32 <= h;
+  const int t_last = h - 1;
+  const bool is_last = (tid == t_last);
+  const bool last_warp = (warp == (t_last >> 5));
+  const unsigned long long tag = (unsigned long long)n0 << 32;
+
+  double inner = 0.0;
+  if (row_on)
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) inner += (double)s_wn[w][tid];
+  if (ncols <= 0) {
+    if (row_on) I.norms[n] = I.delta * (inner + I.bnorm[n]);
+    if (last_warp) {
+      __syncwarp();
+      if (is_last) st_release_u64(my_word, tag);
     }
     return;
   }
-  auto inv = [&](int64_t x) { return x <= wm * G2 ? (x + wm - 1) / wm : G2 + (x - wm * G2); };
-  *lo = inv(W * rank / C);
-  *hi = inv(W * (rank + 1) / C);
+
+  SweepC c;
+  c.I = &I;
+  c.skew = I.skew;
+  c.detab32 = I.detab32;
+  c.phitab32 = I.phitab32;
+  c.lo_row = I.lo_row;
+  c.R = R;
+  c.n = n;
+  c.nslot = n % R;
+  c.sD = (c.nslot >= D) ? c.nslot - D : c.nslot - D + R;
+  c.lane = lane;
+  c.D = D;
+  c.nx = nx;
+  c.ncols = ncols;
+  c.rd = (int)I.rd;
+  c.row_on = row_on;
+  const bool hasD = row_on && n >= D;
+  c.useD = hasD && D >= kPre;  // a delay value kPre steps ahead is not yet written when D < kPre
+  const bool sqon = row_on && n >= D + 1;
+  c.is_last = is_last;
+  c.rowD_in = I.ring + (int64_t)(hasD ? c.sD : 0) * I.stride;
+  c.R1 = I.rowscal32[2 * n];
+  c.R2 = I.rowscal32[2 * n + 1];
+  c.snap = (row_on && I.tstep >= 0 && n % (I.tstep + 1) == 0) ? I.snaps + (int64_t)(n / (I.tstep + 1)) * nx : nullptr;
+  c.hand_out = (lane == 31 && next_on) ? s_hand[warp] : nullptr;
+  c.d1 = I.d1;
+  c.c2 = I.c2;
+  c.c3 = sqon ? I.c3 : z;
+  c.d1l = I.d1lo;
+  c.c2l = I.c2lo;
+  c.c3l = sqon ? I.c3lo : z;
+  const bool direct_d = hasD && D < kPre;
+
+  // state at column D: y = psi[n][D-1] (inner pass), a = psi[n-1][D-1] + its remainder,
+  // the delay value left of storage column 0 (x <= -a)
+  SweepS st;
+  const int s1 = (c.nslot >= 1) ? c.nslot - 1 : c.nslot - 1 + R;
+  st.y = row_on ? I.ring[(int64_t)c.nslot * I.stride + D - 1] : z;
+  st.a_hi = row_on ? I.ring[(int64_t)s1 * I.stride + D - 1] : z;
+  st.a_lo = row_on ? I.lo_edge[n - 1] : z;
+  st.dprev = hasD ? psi_left32(I, n - D, -Dh) : z;
+  st.o_hi = st.o_lo = st.o_hn = z;
+  st.nacc = 0.f;
+  st.dacc = 0.0;
+  st.dout = ((nw % c.rd) + c.rd) % c.rd;
+  st.dpre = (((nw - 2 * D) % c.rd) + c.rd) % c.rd;
+#pragma unroll
+  for (int u = 0; u < kPre; ++u) {
+    st.pq[u] = sweep_fetch(c, u, st.dpre);
+    st.dpre = (st.dpre + 1 == c.rd) ? 0 : st.dpre + 1;
+  }
+
+  // warp 0: the previous band's last row n0-1 (value, remainder) and its delay row
+  // n0-1-D, copied 32 columns at a time into shared memory (cp.async, one chunk ahead)
+  const int np = n0 - 1;
+  const bool pd = (np >= D);
+  auto stage = [&](int ch) {  // warp 0: issue the copies of chunk ch into buffer ch & 1
+    const int b = ch & 1, q = ch * kChunk + lane;
+    if (q < ncols) {
+      cp_async8(&s_pv_hi[b][lane], ring_at(I, np, D + q));
+      cp_async8(&s_pv_lo[b][lane], I.lo_row + D + q);
+      if (pd) cp_async8(&s_pv_d[b][lane + 1], ring_at(I, np - D, q));
+      else s_pv_d[b][lane + 1] = z;
+    }
+    if (lane == 0 && ch * kChunk < ncols) {  // the delay value left of the chunk's first column
+      if (!pd) s_pv_d[b][0] = z;
+      else if (ch == 0) s_pv_d[b][0] = psi_left32(I, np - D, -Dh);
+      else cp_async8(&s_pv_d[b][0], ring_at(I, np - D, ch * kChunk - 1));
+    }
+    cp_async_commit();
+  };
+  auto prev_wait = [&](int cols) {  // warp 0: band c-1's last row has done `cols` columns
+    if (wait_prev && lane == 0)
+      wait_ge_global(prev_word, tag - ((unsigned long long)kBand << 32) + (unsigned long long)(cols < ncols ? cols : ncols),
+                     spin, sync, n0);
+    __syncwarp();
+  };
+  if (warp == 0) {
+    prev_wait(2 * kChunk);
+    stage(0);
+    stage(1);
+    cp_async_wait1();  // chunk 0 is in shared memory
+    __syncwarp();
+  }
+
+  // steps [kfast0, kfast1): every lane marching a column j >= 2D other than the last
+  const int kfast0 = D + 31, kfast1 = ncols - 1;
+  const int kend = (ncols + 31 + kGrp - 1) / kGrp * kGrp;
+  for (int kb = 0; kb < kend; kb += kGrp) {
+    // ---- bookkeeping every kGrp steps
+    __syncwarp();
+    if (warp == 0 && kb > 0 && (kb % kChunk) == 0) {  // chunk ch+1 on its way, chunk ch in place
+      const int ch = kb / kChunk;
+      prev_wait((ch + 2) * kChunk);
+      stage(ch + 1);
+      cp_async_wait1();
+      __syncwarp();
+    }
+    if (last_warp && (kb % kChunk) == 0 && is_last) {  // progress of the band's last row, for band c+1
+      const int done = kb - lane;
+      st_release_u64(my_word, tag + (unsigned long long)(done < 0 ? 0 : (done > ncols ? ncols : done)));
+    }
+    if (warp > 0 && lane == 0) {  // consumer of the warp above
+      __threadfence_block();
+      s_cons[warp] = (kb < ncols) ? kb : ncols;
+      const int need = (kb + 2 * kGrp < ncols) ? kb + 2 * kGrp : ncols;
+      wait_ge_shared(s_prod + warp - 1, need, spin, sync, n0);
+    }
+    if (next_on && lane == 31) {  // producer for the warp below
+      __threadfence_block();
+      const int done = kb - 31;
+      s_prod[warp] = (done < 0) ? 0 : (done > ncols ? ncols : done);
+      const int need = kb + kGrp - 32 - kHandQ + 1;  // the entries this group overwrites were consumed
+      if (need > 0) wait_ge_shared(s_cons + warp + 1, (need < ncols) ? need : ncols, spin, sync, n0);
+    }
+    __syncwarp();
+
+    const bool fast = warp_full && kb >= kfast0 && kb + kGrp <= kfast1;
+    for (int uu = 0; uu < kGrp; uu += kPre) {
+#pragma unroll
+      for (int u = 0; u < kPre; ++u) {
+        const int k = kb + uu + u;
+        // row n-1 at this step's column, from the lane above (its previous step)
+        float2 b_hi = shfl_up2(st.o_hi, 1), b_lo = shfl_up2(st.o_lo, 1), hp = shfl_up2(st.o_hn, 1);
+        if (lane == 0 && k < ncols) {
+          if (warp > 0) {
+            const Hand hd = s_hand[warp - 1][k & (kHandQ - 1)];
+            b_hi = hd.hi;
+            b_lo = hd.lo;
+            hp = hd.hn;
+          } else {
+            const int b = (k / kChunk) & 1, x = k % kChunk;
+            b_hi = s_pv_hi[b][x];
+            b_lo = s_pv_lo[b][x];
+            hp = add(s_pv_d[b][x], s_pv_d[b][x + 1]);
+          }
+        }
+        if (direct_d) {  // D < kPre: the delay value is read at its step
+          const int q = k - lane;
+          st.pq[u].d = ((unsigned)q < (unsigned)ncols) ? *ring_at(I, n - D, q) : z;
+        }
+        if (fast) {
+          if (u == 0) sweep_step<true, 0>(c, st, k, b_hi, b_lo, hp);
+          else sweep_step<true, 1>(c, st, k, b_hi, b_lo, hp);
+        } else {
+          if (u == 0) sweep_step<false, 0>(c, st, k, b_hi, b_lo, hp);
+          else sweep_step<false, 1>(c, st, k, b_hi, b_lo, hp);
+        }
+      }
+    }
+  }
+  __syncwarp();
+  if (next_on && lane == 31) {
+    __threadfence_block();
+    s_prod[warp] = ncols;
+  }
+  if (is_last) st_release_u64(my_word, tag + (unsigned long long)ncols);
+  if (row_on) I.norms[n] = I.delta * (inner + (st.dacc + (double)st.nacc) + I.bnorm[n]);
 }
 
-// ---- TMA bulk copies into shared memory (1D), completion on an mbarrier ----
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  unsigned a = (unsigned)__cvta_generic_to_shared(bar);
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  unsigned a = (unsigned)__cvta_generic_to_shared(bar);
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(a), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  unsigned a = (unsigned)__cvta_generic_to_shared(bar), ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(a), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// copy `bytes` (multiple of 16) from 16-byte aligned global memory to shared memory
-__device__ __forceinline__ void tma_load_1d(void* sdst, const void* gsrc, unsigned bytes, uint64_t* bar) {
-  unsigned d = (unsigned)__cvta_generic_to_shared(sdst), m = (unsigned)__cvta_generic_to_shared(bar);
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(d),
-               "l"(gsrc), "r"(bytes), "r"(m)
-               : "memory");
+// row r of an instance between its rings and a row-major buffer (see RowMap)
+__global__ void k_row_move(RowMap m, int64_t r, float2* buf, int dir) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= m.nx) return;
+  float2* e = (j < m.D) ? m.ring + (r % m.R) * m.stride + j
+                        : m.skew + ((r + j - m.D) % m.rd) * (int64_t)m.R + (r % m.R);
+  if (dir == 0) buf[j] = *e;
+  else *e = (dir == 1) ? buf[j] : make_float2(0.f, 0.f);
 }
 
-// A staged slice: global elements [g0, g1) of a float2 array start at smem
-// element `off` (0 or 1: the copy starts on an even element, 16-byte aligned).
-struct Slice {
-  float2* s;
-  int off;
-  int64_t g0;
-  __device__ __forceinline__ float2 at(int64_t g) const { return s[g - g0 + off]; }
-};
-
-// plan the copy of global elements [g0, g1) into `dst`: the copy starts on an
-// even element (16-byte aligned) and moves an even number of elements
-struct Copy {
-  float2* dst;
-  const float2* src;
-  unsigned bytes;
-};
-__device__ __forceinline__ Copy plan_copy(Slice& sl, float2* dst, const float2* src, int64_t g0, int64_t g1) {
-  const int64_t a = g0 & ~int64_t(1), b = (g1 + 1) & ~int64_t(1);
-  sl.s = dst;
-  sl.off = (int)(g0 - a);
-  sl.g0 = g0;
-  return Copy{dst, src + a, (unsigned)((b - a) * sizeof(float2))};
+cudaError_t launch_row_move(const RowMap& m, int64_t r, float2* buf, int dir, cudaStream_t s) {
+  if (m.nx <= 0) return cudaSuccess;
+  k_row_move<<<(unsigned)((m.nx + 255) / 256), 256, 0, s>>>(m, r, buf, dir);
+  return cudaGetLastError();
 }
 
-constexpr int kBlk = 2048;        // bulk columns staged per block
-constexpr int kStageCols = kBlk + 4;
-
-__global__ void __launch_bounds__(kF32Threads, 1)
+__global__ void __launch_bounds__(kF32Threads, 2)
     k_march_f32c(const InstDesc* __restrict__ insts, const WorkItem* __restrict__ items, int nitems,
                  unsigned int* queue, SyncWords* sync) {
-  extern __shared__ __align__(128) float2 smem[];
-  __shared__ float2 s_last[kF32Threads];
-  __shared__ int s_len[kF32Threads];
-  __shared__ float2 s_carry[2];  // carry into a block, by block parity: a block's pass B reads one slot
-                                 // while the thread ending that block writes the other
-  __shared__ float2 s_halo[kMaxTrunc];
-  __shared__ float s_red[2][kF32Threads / 32];
-  __shared__ int s_inst;
-  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ Hand s_hand[kWarps - 1][kHandQ];
+  __shared__ int s_prod[kWarps], s_cons[kWarps];
+  __shared__ float2 s_pv_hi[2][kChunk], s_pv_lo[2][kChunk], s_pv_d[2][kChunk + 1];
+  __shared__ float s_wn[kWarps][kBand];
+  __shared__ float2 s_scP[kWarps], s_scY[kWarps];
+  __shared__ float2 s_ylast;
+  __shared__ int s_item;
   __shared__ __align__(16) InstDesc s_I;  // the instance's descriptor: no global store can alias it
 
   const int tid = threadIdx.x;
-  const unsigned rank = cluster_rank(), C = cluster_size();
-  // shared memory: 6 staging slices, then the pair sums of the CTA's columns
-  float2* st_a1 = smem;
-  float2* st_ad = st_a1 + kStageCols;
-  float2* st_ad1 = st_ad + kStageCols;
-  float2* st_lo = st_ad1 + kStageCols;
-  float2* st_de = st_lo + kStageCols;
-  float2* st_ph = st_de + kStageCols;
-  float2* o_hi = st_ph + kStageCols;  // block results: hi (or parked S), remainder (or parked a_hi)
-  float2* o_e = o_hi + kStageCols;
-  float2* hs_base = o_e + kStageCols;
-  if (tid == 0) mbar_init(&s_bar, 1);
-  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-  __syncthreads();
-  unsigned bar_phase = 0;
-
   for (;;) {
-    // the cluster's next work item: one wide instance for the whole cluster, or
-    // up to C narrow instances, one per CTA ("solo": CTA barriers only)
-    if (rank == 0 && tid == 0) {
-      unsigned q = atomicAdd(queue, 1u);
-      s_inst = (q < (unsigned)nitems) ? (int)q : -1;
+    // the next band stream: bands stream, stream + g, ... of one instance
+    if (tid == 0) {
+      const unsigned q = atomicAdd(queue, 1u);
+      s_item = (q < (unsigned)nitems) ? (int)q : -1;
     }
-    cluster_sync_all();
-    const int item = ld_dsmem_i32(&s_inst, 0);
-    cluster_sync_all();  // s_inst is read by every CTA before rank 0 may overwrite it
+    __syncthreads();
+    const int item = s_item;
     if (item < 0) break;
-    const WorkItem& Wk = items[item];
-    const bool solo = Wk.solo != 0;
-    const int inst = solo ? ((rank < (unsigned)Wk.count) ? Wk.inst[rank] : -1) : Wk.inst[0];
-    const unsigned rank_e = solo ? 0u : rank, C_e = solo ? 1u : C;
-    if (inst >= 0) {
-      const int* src = reinterpret_cast<const int*>(&insts[inst]);
+    const WorkItem Wk = items[item];
+    {
+      const int* src = reinterpret_cast<const int*>(&insts[Wk.inst]);
       int* dst = reinterpret_cast<int*>(&s_I);
       for (int k = tid; k < (int)(sizeof(InstDesc) / sizeof(int)); k += kF32Threads) dst[k] = src[k];
     }
     __syncthreads();
-    if (inst >= 0 && s_I.range[0] < s_I.range[1]) {
+    if (s_I.range[0] < s_I.range[1]) {
       const InstDesc& I = s_I;
-      const int64_t n_begin = I.range[0], n_end = I.range[1];
-      const int D = I.D;
-      int64_t j_lo, j_hi;
-      cta_range(I, (int)rank_e, (int)C_e, &j_lo, &j_hi);
-      const int64_t G2 = (2 * (int64_t)D < I.nx) ? 2 * (int64_t)D : I.nx;
-      const int64_t h0 = (j_lo - I.khalo > 0) ? j_lo - I.khalo : 0;
-      const int nh = (int)(j_lo - h0);
-      const bool reuse = (j_hi - j_lo + nh <= I.smem_cols);  // pair sums kept in shared memory
-      float2* hs = reuse ? hs_base : nullptr;
-
-      int slot = (int)(n_begin % I.R);
-      int64_t snap_ctr = (I.tstep >= 0) ? n_begin % (I.tstep + 1) : -1;
-      for (int64_t n = n_begin; n < n_end; ++n) {
-        auto back = [&](int k) { int t = slot - k; return t < 0 ? t + I.R : t; };
-        RowF R;
-        R.n = n;
-        R.nslot = slot;
-        R.row1 = I.ring + (int64_t)back(1) * I.stride;
-        R.rowD = (n >= D) ? I.ring + (int64_t)back(D) * I.stride : nullptr;
-        R.rowD1 = (n >= D + 1) ? I.ring + (int64_t)back(D + 1) * I.stride : nullptr;
-        float2* row0 = I.ring + (int64_t)slot * I.stride;
-        float2* snap = (snap_ctr == 0) ? I.snaps + (n / (I.tstep + 1)) * I.nx : nullptr;
-        R.R1 = I.rowscal32[2 * n];
-        R.R2 = I.rowscal32[2 * n + 1];
-        R.hs = hs;
-        R.hbase = h0;
-        R.cold = (n == n_begin);
-        float2* es_rd = I.lo + (int64_t)((n - 1) & 1) * I.lo_pitch;
-        float2* es_wr = I.lo + (int64_t)(n & 1) * I.lo_pitch;
-        float nacc = 0.f;
-
-        // carry into the CTA's first column: psi(-a) for the first CTA, else the
-        // recurrence over khalo columns to its left (warp 0)
-        if (tid < 32 && j_lo < j_hi) {
-          if (tid == 0 && j_lo == 0) es_rd[0] = I.bnd32[2 * (n - 1) + 1];  // thread 0 owns column 0
-          for (int c = tid; c < nh; c += 32) {
-            float2 ah;
-            float2 S = rhs32(I, R, h0 + c, &ah);
-            s_halo[c] = add(ah, S);
-          }
-          __syncwarp();
-          if (tid == 0) {
-            float2 yh = (h0 == 0) ? I.bnd32[2 * n] : f2(0.f, 0.f);
-            for (int c = 0; c < nh; ++c) yh = fmac(I.c2lo, yh, fmac(I.c2, yh, s_halo[c]));
-            s_carry[0] = yh;
-          }
+      const int g = Wk.g, r = Wk.stream;
+      const int64_t nb = I.range[0], ne = I.range[1];
+      unsigned long long* gdone = I.bsync;        // rows whose inner columns are complete
+      unsigned long long* prog = I.bsync + 1;     // per stream: (first row of its band << 32) + columns
+      for (int64_t n0 = nb + (int64_t)r * kBand; n0 < ne; n0 += (int64_t)g * kBand) {
+        const int h = (int)((ne - n0 < kBand) ? ne - n0 : kBand);
+        const bool first = (n0 == nb);
+        if (tid == 0 && !first) wait_ge_global(gdone, (unsigned long long)n0, I.spin, sync, n0);
+        __syncthreads();  // also: every warp has finished the previous band's sweep
+        if (tid < kWarps) {
+          s_prod[tid] = 0;
+          s_cons[tid] = 0;
         }
-
-        // blocks: first the columns of -a < x <= 3a (read in place, cost-weighted
-        // over the threads), then x > 3a in staged blocks of kBlk
-        // the six staged slices of a bulk block [b0, b1): rows n-1, n-D, n-D-1, the
-        // remainders of row n-1, and the source tables; thread 0 arms the barrier
-        // with their bytes and issues the copies
-        auto stage = [&](int64_t b0, int64_t b1, Slice& A1, Slice& AD, Slice& AD1, Slice& LO, Slice& DE,
-                         Slice& PH) {
-          const int64_t ib = n - b1 + D;  // detab index of the block's last column
-          const int64_t ilo = (ib > 0) ? ib : 0, ihi = n - b0 + D;        // detab [ilo, ihi)
-          const int64_t plo = (ib - D > 0) ? ib - D : 0, phi_ = n - b0;  // phitab [plo, phi_)
-          Copy cp[6];
-          cp[0] = plan_copy(A1, st_a1, R.row1, b0 - 1, b1);
-          cp[1] = R.rowD ? plan_copy(AD, st_ad, R.rowD, b0 - D - 1, b1 - D) : Copy{nullptr, nullptr, 0u};
-          cp[2] = (R.rowD1 && (!hs || R.cold)) ? plan_copy(AD1, st_ad1, R.rowD1, b0 - D - 1, b1 - D)
-                                               : Copy{nullptr, nullptr, 0u};
-          cp[3] = plan_copy(LO, st_lo, es_rd, b0, b1);
-          cp[4] = (ihi > ilo) ? plan_copy(DE, st_de, I.detab32, ilo, ihi) : Copy{nullptr, nullptr, 0u};
-          cp[5] = (phi_ > plo) ? plan_copy(PH, st_ph, I.phitab32, plo, phi_) : Copy{nullptr, nullptr, 0u};
-          if (tid == 0) {
-            unsigned bytes = 0;
-            for (int k = 0; k < 6; ++k) bytes += cp[k].bytes;
-            asm volatile("fence.proxy.async;\n" ::: "memory");
-            mbar_expect_tx(&s_bar, bytes);
-            for (int k = 0; k < 6; ++k)
-              if (cp[k].bytes) tma_load_1d(cp[k].dst, cp[k].src, cp[k].bytes, &s_bar);
-          }
-        };
-        // a bulk block's copies may be issued while the block before it finishes
-        // (pass B and the stores read only the output buffers)
-        bool pre = false;
-        Slice pA1, pAD, pAD1, pLO, pDE, pPH;
-        int blk = 0;  // block index within the row (selects the carry slot)
-        int64_t c0 = j_lo;
-        while (c0 < j_hi) {
-          const bool gen = (c0 < G2);
-          const int64_t c1 = gen ? ((j_hi < G2) ? j_hi : G2) : ((c0 + kBlk < j_hi) ? c0 + kBlk : j_hi);
-          const int64_t len = c1 - c0;
-          // this thread's segment of the block
-          int64_t t0, t1;
-          if (!gen) {
-            const int64_t seg = ((len + kF32Threads - 1) / kF32Threads) | 1;
-            t0 = c0 + (int64_t)tid * seg;
-            if (t0 > c1) t0 = c1;
-            t1 = (t0 + seg < c1) ? t0 + seg : c1;
-          } else if (len < kF32Threads) {
-            // fewer columns than threads: one column each on the first `len` threads, so
-            // that every carry in pass B crosses only non-empty segments
-            t0 = (tid < len) ? c0 + tid : c1;
-            t1 = (tid < len) ? t0 + 1 : c1;
-          } else {
-            t0 = c0 + len * tid / kF32Threads;
-            t1 = c0 + len * (tid + 1) / kF32Threads;
-          }
-          s_len[tid] = (int)(t1 - t0);
-
-          Slice A1, AD, AD1, LO, DE, PH;
-          if (!gen) {
-            if (pre) {
-              A1 = pA1;
-              AD = pAD;
-              AD1 = pAD1;
-              LO = pLO;
-              DE = pDE;
-              PH = pPH;
-              pre = false;
-            } else {
-              stage(c0, c1, A1, AD, AD1, LO, DE, PH);
-            }
-            // bounded wait for the copies
-            long long tw = clock64();
-            while (!mbar_try_wait(&s_bar, bar_phase)) {
-              if (clock64() - tw > 4000000000LL) {
-                if (atomicCAS(&sync->status, 0u, (unsigned)FDTD_ERR_TIMEOUT) == 0u) sync->where = n;
-                break;
-              }
-            }
-            bar_phase ^= 1u;
-          }
-
-          // pass A: the segment from a zero carry; its first kfix columns are
-          // parked (S, a_hi) until pass B adds the carry.  Results of a staged
-          // block go to shared memory (o_hi: hi or parked S, o_e: remainder or
-          // parked a_hi) and leave in coalesced stores after pass B; a block of
-          // -a < x <= 3a writes its few columns in place.
-          float2 y = f2(0.f, 0.f);
-          int v = 0;
-          float2* oh = gen ? row0 + c0 : o_hi;      // column j at oh[j - c0]
-          float2* oe = gen ? es_wr + c0 + 1 : o_e;  // remainder of column j at oe[j - c0]
-          auto emit = [&](int64_t j, float2 ah, float2 S) {
-            if (v < I.kfix) {
-              oh[j - c0] = S;
-              oe[j - c0] = ah;
-              y = add(ah, S);
-            } else {
-              float2 sv, e;
-              two_sum(ah.x, S.x, sv.x, e.x);
-              two_sum(ah.y, S.y, sv.y, e.y);
-              oh[j - c0] = sv;
-              oe[j - c0] = e;
-              const float wt = (j == I.nx - 1) ? 0.5f : 1.0f;
-              nacc = fmaf(wt * sv.x, sv.x, nacc);
-              nacc = fmaf(wt * sv.y, sv.y, nacc);
-              y = sv;
-            }
-            ++v;
-          };
-          if (gen) {
-            for (int64_t j = t0; j < t1; ++j) {
-              float2 ah;
-              float2 S = rhs_general32(I, n, R.nslot, j, R.R2, &ah);
-              if (j == 0) ah = I.bnd32[2 * (n - 1)];
-              S = add(S, __ldcg(es_rd + j));
-              emit(j, ah, fmac(I.c2lo, y, fmac(I.c2, y, S)));
-            }
-          } else {
-            // block-relative 32-bit offsets: column j = c0 + k
-            const bool d1 = (R.rowD1 != nullptr), dd = (R.rowD != nullptr);
-            const bool use_hs = hs && !R.cold;
-            const float2* a1s = A1.s + A1.off;                 // a_hi(k) = a1s[k], b(k) = a1s[k+1]
-            const float2* ads = AD.s + AD.off;                 // row n-D: ads[k], ads[k+1]
-            const float2* ad1s = AD1.s + AD1.off;
-            const float2* los = LO.s + LO.off;
-            const int kde = (int)(n - c0 - 1 + D);             // i(k) = kde - k
-            const float2* des = DE.s + DE.off - DE.g0;         // detab32[i] = des[i]
-            const float2* phs = PH.s + PH.off - PH.g0;         // phitab32[i - D] = phs[i - D]
-            float2* hsb = hs ? hs + (c0 - h0) : nullptr;
-            const int k0 = (int)(t0 - c0), k1 = (int)(t1 - c0);
-            const int klast = (int)(I.nx - 1 - c0);
-            const float2 d1c = I.d1, c2c = I.c2, c3c = I.c3, R1 = R.R1, R2 = R.R2;
-            const float2 d1l = I.d1lo, c2l = I.c2lo, c3l = I.c3lo;
-            const int kfix = I.kfix;
-            for (int k = k0; k < k1; ++k) {
-              const float2 a = a1s[k], b = a1s[k + 1];
-              float2 S = mulc(d1c, a);
-              S = fmac(c2c, b, S);
-              float2 L = fmac(c2l, b, mulc(d1l, a));
-              if (dd) {
-                const float2 hn = add(ads[k], ads[k + 1]);
-                if (d1) {
-                  const float2 sq = add(hn, use_hs ? hsb[k] : add(ad1s[k], ad1s[k + 1]));
-                  S = fmac(c3c, sq, S);
-                  L = fmac(c3l, sq, L);
-                }
-                if (hsb) hsb[k] = hn;
-              }
-              S = add(S, L);
-              const int i = kde - k;
-              if (i >= 0) S = fmac(R1, des[i], S);
-              if (i >= D) S = fmac(R2, phs[i - D], S);
-              S = add(S, los[k]);
-              S = fmac(c2l, y, fmac(c2c, y, S));
-              if (v < kfix) {
-                o_hi[k] = S;
-                o_e[k] = a;
-                y = add(a, S);
-              } else {
-                float2 sv, e;
-                two_sum(a.x, S.x, sv.x, e.x);
-                two_sum(a.y, S.y, sv.y, e.y);
-                o_hi[k] = sv;
-                o_e[k] = e;
-                const float wt = (k == klast) ? 0.5f : 1.0f;
-                nacc = fmaf(wt * sv.x, sv.x, nacc);
-                nacc = fmaf(wt * sv.y, sv.y, nacc);
-                y = sv;
-              }
-              ++v;
-            }
-          }
-          s_last[tid] = (t0 < t1) ? y : f2(0.f, 0.f);
-          __syncthreads();
-          // the staging slices are free: issue the next bulk block's copies now
-          if (!gen && c1 < j_hi) {
-            stage(c1, (c1 + kBlk < j_hi) ? c1 + kBlk : j_hi, pA1, pAD, pAD1, pLO, pDE, pPH);
-            pre = true;
-          }
-
-          // pass B: carry from the threads before (the block's carry-in for thread 0)
-          if (t0 < t1) {
-            float2 carry = f2(0.f, 0.f), ap = f2(1.f, 0.f);
-            for (int s = 1; s <= tid + 1; ++s) {
-              if (tid - s >= 0) {
-                carry = fmac(ap, s_last[tid - s], carry);
-                const int lu = s_len[tid - s];
-                ap = mulc(ap, (lu <= kF32MaxTrunc) ? I.c2pow[lu] : f2(0.f, 0.f));
-                if (ap.x * ap.x + ap.y * ap.y < 2.2e-16f) break;  // (2^-26)^2
-              } else {
-                carry = fmac(ap, s_carry[blk & 1], carry);
-              }
-            }
-            const int nf = (I.kfix < (int)(t1 - t0)) ? I.kfix : (int)(t1 - t0);
-            const int kb = (int)(t0 - c0), klast = (int)(I.nx - 1 - c0), kend = (int)(t1 - 1 - c0);
-            float2 ylast = y;
-#pragma unroll 4
-            for (int u = 0; u < nf; ++u) {  // only the kfix parked columns take the carry
-              const int k = kb + u;
-              const float2 S = fmac(I.c2powlo[u + 1], carry, fmac(I.c2pow[u + 1], carry, oh[k]));
-              const float2 A = oe[k];
-              float2 sv, e;
-              two_sum(A.x, S.x, sv.x, e.x);
-              two_sum(A.y, S.y, sv.y, e.y);
-              oh[k] = sv;
-              oe[k] = e;
-              const float wt = (k == klast) ? 0.5f : 1.0f;
-              nacc = fmaf(wt * sv.x, sv.x, nacc);
-              nacc = fmaf(wt * sv.y, sv.y, nacc);
-              if (k == kend) ylast = sv;
-            }
-            if (t1 == c1) s_carry[(blk + 1) & 1] = ylast;  // carry into the next block
-            if (gen && snap)
-              for (int64_t jj = t0; jj < t1; ++jj) snap[jj] = row0[jj];
-          }
-          __syncthreads();  // block results complete
-          if (!gen) {  // coalesced stores of the block
-            float2* r0 = row0 + c0;
-            float2* ew = es_wr + c0 + 1;
-            float2* sp = snap ? snap + c0 : nullptr;
-            for (int k = tid; k < (int)len; k += kF32Threads) {
-              const float2 h = o_hi[k];
-              r0[k] = h;
-              ew[k] = o_e[k];
-              if (sp) sp[k] = h;
-            }
-            __syncthreads();  // staging and output buffers free for the next block
-          }
-          c0 = c1;
-          ++blk;
-        }
-
-        // norm: FP32 within a warp, FP64 across warps and CTAs
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) nacc += __shfl_down_sync(0xffffffffu, nacc, o);
-        if ((tid & 31) == 0) s_red[n & 1][tid >> 5] = nacc;
-        if (solo) __syncthreads();
-        else cluster_sync_all();
-        if (rank_e == 0 && tid < 32) {
-          // warp 0 of rank 0 gathers every warp's partial (local or over DSMEM) at once
-          constexpr int nw = kF32Threads / 32;
-          const int tot = (int)C_e * nw;
-          double t = 0.0;
-          for (int q = tid; q < tot; q += 32) {
-            const float* pw = &s_red[n & 1][q % nw];
-            t += (double)(solo ? *pw : ld_dsmem_f32(pw, (unsigned)(q / nw)));
-          }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-          if (tid == 0) I.norms[n] = I.delta * (t + I.bnorm[n]);
-        }
-        slot = (slot + 1 == I.R) ? 0 : slot + 1;
-        if (snap_ctr >= 0) snap_ctr = (snap_ctr == I.tstep) ? 0 : snap_ctr + 1;
+        inner_rows(I, n0, h, s_wn, s_scP, s_scY, &s_ylast);
+        __syncthreads();
+        if (tid == 0) st_release_u64(gdone, (unsigned long long)(n0 + h));
+        sweep(I, (int)n0, h, !first && g > 1, prog + (r + g - 1) % g, prog + r, sync, s_hand, s_prod, s_cons,
+              s_pv_hi, s_pv_lo, s_pv_d, s_wn);
       }
     }
-    cluster_sync_all();  // the item is complete before any CTA of the cluster moves on
+    __syncthreads();  // s_item and s_I are read by every thread before they are rewritten
   }
 }
 
@@ -686,40 +752,25 @@ cudaError_t launch_advance(InstDesc* insts, int ninst, int64_t rows, cudaStream_
   return cudaGetLastError();
 }
 
-size_t march_f32c_smem(int64_t cols) { return sizeof(float2) * (size_t)(8 * kStageCols + cols); }
-
-int march_f32c_max_clusters(int csize, size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_march_f32c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return -1;
-  if (csize > 8) cudaFuncSetAttribute(k_march_f32c, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(csize);
-  cfg.blockDim = dim3(kF32Threads);
-  cfg.dynamicSmemBytes = smem;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = csize;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  int n = 0;
-  e = cudaOccupancyMaxActiveClusters(&n, (const void*)k_march_f32c, &cfg);
-  return e == cudaSuccess ? n : -1;
+int march_f32c_blocks_per_sm() {
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_march_f32c, kF32Threads, 0) != cudaSuccess) return 0;
+  return per;
 }
 
+// every CTA resident (cooperative): a band stream may wait on a stream later in the
+// queue only while fewer CTAs than its gang are busy, so grid >= the widest gang
+// leaves no wait without a CTA to end it
 cudaError_t launch_march_f32c(const InstDesc* insts, const WorkItem* items, int nitems, unsigned int* queue,
-                              SyncWords* sync, int nclusters, int csize, size_t smem, cudaStream_t s) {
+                              SyncWords* sync, int grid, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(nclusters * csize);
+  cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kF32Threads);
-  cfg.dynamicSmemBytes = smem;
+  cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = csize;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_march_f32c, insts, items, nitems, queue, sync);

@@ -5,12 +5,16 @@
 //
 //   header (kStateHeaderBytes)                 parameters and counts, below
 //   rows   rows_kept x nx x elem_bytes          rows rows_done-rows_kept .. rows_done-1,
-//                                               in the plan's own storage format
-//                                               (complex128, double-float pairs or
-//                                               complex64), so that a resumed march
-//                                               is bitwise the uninterrupted one
-//   lo     2 x lo_pitch x 8 B (complex64 only)  the TwoSum remainders of the last two
-//                                               rows, carried along characteristics
+//                                               row-major in the plan's own element
+//                                               format (complex128, double-float pairs
+//                                               or complex64), so that a resumed march
+//                                               is bitwise the uninterrupted one (a
+//                                               complex64 row is gathered from its two
+//                                               rings through the plan's staging row)
+//   lo     lo_elems x 8 B (complex64 only)      the TwoSum remainders the next row adds
+//                                               along its characteristics: inner columns
+//                                               (two row slots), the other columns of the
+//                                               last row, column D-1 of every row
 //   norms  rows_done x 8 B                      N(n) of every row so far
 //
 // A batched plan's checkpoint is one such record per instance, back to back.
@@ -28,7 +32,7 @@ using fdtd::cd;
 namespace {
 
 constexpr uint32_t kStateMagic = 0x53544446u;  // "FDTS"
-constexpr uint32_t kStateVersion = 1;
+constexpr uint32_t kStateVersion = 2;
 constexpr size_t kStateHeaderBytes = 256;
 
 struct StateHeader {
@@ -50,6 +54,7 @@ struct InstView {
   int64_t lo_elems;
   double* norms;
   int64_t* rows_done;
+  bool gathered;  // complex64: rows are spread over two rings; copied through P's staging row
 };
 
 InstView view(fdtd_plan_s* P, int i) {
@@ -62,9 +67,10 @@ InstView view(fdtd_plan_s* P, int i) {
     v.R = b.R;
     v.elem = sizeof(float2);
     v.lo = P->ws + b.off_lo;
-    v.lo_elems = 2 * ((b.p.nx + 4 + 7) / 8 * 8);
+    v.lo_elems = b.lo_elems;
     v.norms = reinterpret_cast<double*>(P->ws + b.off_norms);
     v.rows_done = &b.rows_done;
+    v.gathered = true;
   } else {
     v.p = &P->p;
     v.ring = P->ws + P->off_ring;
@@ -75,6 +81,7 @@ InstView view(fdtd_plan_s* P, int i) {
     v.lo_elems = 0;
     v.norms = reinterpret_cast<double*>(P->ws + P->off_norms);
     v.rows_done = &P->rows_done;
+    v.gathered = false;
   }
   return v;
 }
@@ -99,7 +106,8 @@ int64_t state_bytes(fdtd_plan_s* P, int inst) {
 
 // copy instance `inst`'s record into dst (any memory); the stream is synchronised
 fdtd_status state_readout(fdtd_plan_s* P, int inst, void* dst, int64_t dst_bytes, cudaStream_t s) {
-  InstView v = view(P, P->batched ? inst : 0);
+  if (!P->batched) inst = 0;
+  InstView v = view(P, inst);
   const int64_t done = *v.rows_done;
   const int64_t need = record_bytes(v, done);
   if (!dst || dst_bytes < need) return FDTD_ERR_INVALID_ARG;
@@ -133,7 +141,13 @@ fdtd_status state_readout(fdtd_plan_s* P, int inst, void* dst, int64_t dst_bytes
   d += kStateHeaderBytes;
   const size_t row_bytes = v.elem * (size_t)v.p->nx;
   for (int64_t r = done - h.rows_kept; r < done && e == cudaSuccess; ++r) {
-    e = cudaMemcpyAsync(d, v.ring + v.elem * (size_t)((r % v.R) * v.stride), row_bytes, cudaMemcpyDefault, s);
+    if (v.gathered) {
+      float2* stage = reinterpret_cast<float2*>(P->ws + P->off_stage);
+      e = fdtd::launch_row_move(row_map(P, inst), r, stage, 0, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(d, stage, row_bytes, cudaMemcpyDefault, s);
+    } else {
+      e = cudaMemcpyAsync(d, v.ring + v.elem * (size_t)((r % v.R) * v.stride), row_bytes, cudaMemcpyDefault, s);
+    }
     d += row_bytes;
   }
   if (v.lo_elems && e == cudaSuccess) {
@@ -173,7 +187,13 @@ fdtd_status state_restore(fdtd_plan_s* P, const void* blob, int64_t nbytes, cuda
     const size_t row_bytes = v.elem * (size_t)p.nx;
     cudaError_t e = cudaSuccess;
     for (int64_t r = h.rows_done - h.rows_kept; r < h.rows_done && e == cudaSuccess; ++r) {
-      e = cudaMemcpyAsync(v.ring + v.elem * (size_t)((r % v.R) * v.stride), d, row_bytes, cudaMemcpyDefault, s);
+      if (v.gathered) {
+        float2* stage = reinterpret_cast<float2*>(P->ws + P->off_stage);
+        e = cudaMemcpyAsync(stage, d, row_bytes, cudaMemcpyDefault, s);
+        if (e == cudaSuccess) e = fdtd::launch_row_move(row_map(P, i), r, stage, 1, s);
+      } else {
+        e = cudaMemcpyAsync(v.ring + v.elem * (size_t)((r % v.R) * v.stride), d, row_bytes, cudaMemcpyDefault, s);
+      }
       d += row_bytes;
     }
     if (v.lo_elems && e == cudaSuccess) {

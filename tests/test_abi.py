@@ -56,8 +56,8 @@ def _cfg(F, **kw):
 
 @pytest.mark.parametrize("kw", [dict(D=7), dict(D=0), dict(nx=6), dict(nt=0), dict(delta=0.0), dict(gamma=-1.0),
                                 dict(init_cond=0), dict(init_cond=6), dict(init_cond=5, alpha2=0.0), dict(init_cond=3, alpha=0.0), dict(init_cond=4, sigma=0.0),
-                                dict(tstep=-2), dict(cluster_ctas=9), dict(cluster_ctas=-1), dict(mid_weight=-3),
-                                dict(mid_weight=5000), dict(precision=1, cluster_ctas=9), dict(spin_cycles=-1),
+                                dict(tstep=-2), dict(cluster_ctas=65), dict(cluster_ctas=-1), dict(mid_weight=-3),
+                                dict(mid_weight=5000), dict(precision=1, cluster_ctas=65), dict(spin_cycles=-1),
                                 dict(precision=1, spin_cycles=-5)])
 def test_plan_rejects_bad_params(F, kw):
     L = F.lib()

@@ -17,15 +17,15 @@ def test_tune_picks_fastest_and_caches(tmp_path):
 
     def timer(configs, cl, w, rows):
         calls.append((cl, w))
-        return 10.0 + abs(cl - 4) + abs(w - 32) / 8.0  # fastest at (4, 32)
+        return 10.0 + abs(cl - 16) + abs(w - 32) / 8.0  # fastest at (16, 32)
 
     path = str(tmp_path / "cache.json")
     ch = A.tune(c, rows=64, cache_path=path, timer=timer)
-    assert (ch.cluster_ctas, ch.mid_weight) == (4, 32)
+    assert (ch.cluster_ctas, ch.mid_weight) == (16, 32)
     assert sorted(calls) == sorted(A.CANDIDATES) and len(ch.table) == len(A.CANDIDATES)
     calls.clear()
     again = A.tune(c, rows=64, cache_path=path, timer=timer)
-    assert calls == [] and (again.cluster_ctas, again.mid_weight) == (4, 32) and again.key == ch.key
+    assert calls == [] and (again.cluster_ctas, again.mid_weight) == (16, 32) and again.key == ch.key
     A.tune(c, rows=64, cache_path=path, timer=timer, refresh=True)
     assert len(calls) == len(A.CANDIDATES)
 
