@@ -43,7 +43,7 @@ fdtd_status cuda_fail(fdtd_plan_s* p, cudaError_t e, const char* where) {
 // stream per total / (grid share / 8) updates of its own
 constexpr int kGangShare = 16;
 constexpr int kGangDefault = 32;  // band streams of the largest instance
-constexpr int kTablePad = 64;     // zero entries after the FP32 source tables (>= 32 + prefetch distance)
+constexpr int kTablePad = 64;     // zero entries beyond the sweep's reach (>= 32 + 8 + prefetch distance)
 constexpr long long kSpinDefault = 4000000000LL;  // about 2 s at GB300 clocks
 
 fdtd_status validate(const fdtd_params& p) {
@@ -150,11 +150,13 @@ fdtd_status batch_plan_fill(fdtd_plan_s* P, const fdtd_params* pin, int32_t n, v
     b.off_norms = off;    off = align_up(off + sizeof(double) * (size_t)p.nt);
     b.off_hscr = off;     off = align_up(off + sizeof(cd) * (size_t)p.nt);
     b.off_etab32 = off;   off = align_up(off + sizeof(float2) * (size_t)p.nt);
-    // FP32 source tables with a zero entry at index -1 and kTablePad zeros after the end:
-    // the sweep indexes them without bounds tests (out of the light cone they give 0)
-    b.off_phi32 = off;    off = align_up(off + sizeof(float2) * (size_t)(b.nphi + 1 + kTablePad));
+    // FP32 source tables padded with zeros on both sides: the sweep walks them without
+    // bounds tests (an index below 0, out of the light cone, gives 0)
+    b.padl_e = (p.nx - p.D) + kTablePad;
+    b.padl_f = (p.nx - p.D) + p.D + kTablePad;
+    b.off_phi32 = off;    off = align_up(off + sizeof(float2) * (size_t)(b.padl_f + b.nphi + kTablePad));
     b.off_rowscal32 = off; off = align_up(off + 2 * sizeof(float2) * (size_t)p.nt);
-    b.off_detab32 = off;  off = align_up(off + sizeof(float2) * (size_t)(p.nt + p.D + 1 + kTablePad));
+    b.off_detab32 = off;  off = align_up(off + sizeof(float2) * (size_t)(b.padl_e + p.nt + p.D + kTablePad));
     b.off_lo = off;       off = align_up(off + sizeof(float2) * (size_t)b.lo_elems);
     b.off_bnd = off;      off = align_up(off + sizeof(float2) * 2 * (size_t)p.nt);
     b.off_bnorm = off;    off = align_up(off + sizeof(double) * (size_t)p.nt);
@@ -204,9 +206,9 @@ fdtd_status batch_set_boundary(fdtd_plan_s* P, int32_t source, const void* table
     if (e == cudaSuccess && b.nsnap)
       e = cudaMemsetAsync(P->ws + b.off_snaps, 0, sizeof(float2) * (size_t)b.nsnap * (size_t)p.nx, s);
     if (e == cudaSuccess)
-      e = cudaMemsetAsync(P->ws + b.off_phi32, 0, sizeof(float2) * (size_t)(b.nphi + 1 + kTablePad), s);
+      e = cudaMemsetAsync(P->ws + b.off_phi32, 0, sizeof(float2) * (size_t)(b.padl_f + b.nphi + kTablePad), s);
     if (e == cudaSuccess)
-      e = cudaMemsetAsync(P->ws + b.off_detab32, 0, sizeof(float2) * (size_t)(p.nt + p.D + 1 + kTablePad), s);
+      e = cudaMemsetAsync(P->ws + b.off_detab32, 0, sizeof(float2) * (size_t)(b.padl_e + p.nt + p.D + kTablePad), s);
     if (e != cudaSuccess) return cuda_fail(P, e, "cudaMemsetAsync");
     if (source == FDTD_BOUNDARY_TABLE) {
       e = cudaMemcpyAsync(P->ws + b.off_etab, tab, sizeof(cd) * (size_t)p.nt, cudaMemcpyDeviceToDevice, s);
@@ -292,8 +294,8 @@ fdtd_status batch_set_boundary(fdtd_plan_s* P, int32_t source, const void* table
     d.etab = at<cd>(P, b.off_etab);
     d.phitab = at<cd>(P, b.off_phi);
     d.etab32 = at<float2>(P, b.off_etab32);
-    d.phitab32 = at<float2>(P, b.off_phi32) + 1;
-    d.detab32 = at<float2>(P, b.off_detab32) + 1;
+    d.phitab32 = at<float2>(P, b.off_phi32) + b.padl_f;
+    d.detab32 = at<float2>(P, b.off_detab32) + b.padl_e;
     d.rowscal32 = at<float2>(P, b.off_rowscal32);
     d.bnd32 = at<float2>(P, b.off_bnd);
     d.bnorm = at<double>(P, b.off_bnorm);

@@ -248,8 +248,8 @@ struct InstDesc {
   const cd* etab;          // FP64 tables
   const cd* phitab;
   const float2* etab32;    // FP32 copies
-  const float2* phitab32;  // [-1] and the entries after the table's end are 0
-  const float2* detab32;   // [-1] and the entries after the table's end are 0
+  const float2* phitab32;  // zero-padded: [-(nx - D) - D - 64, 0) and 64 entries past the end
+  const float2* detab32;   // zero-padded: [-(nx - D) - 64, 0) and 64 entries past the end
   const float2* rowscal32;
   const float2* bnd32;     // 2 per row: psi(-a, n delta) as FP32 hi and lo
   const double* bnorm;     // per row: (1/2)|psi(-a, n delta)|^2
@@ -272,6 +272,7 @@ struct fdtd_batch_inst {
       off_detab32, off_ring, off_skew, off_snaps, off_lo, off_bsync, off_bnd, off_bnorm;
   int64_t stride, nphi, nsnap;
   int64_t dpad, nxpad, lo_elems;  // remainders: lo_in 2 x dpad, lo_row nxpad, lo_edge nt
+  int64_t padl_e, padl_f;         // zero entries before the FP32 detab and phi tables
   int R, g;                       // ring rows; CTAs that march the instance together
   fdtd::cd c1, c2, c3, cs, gs;
   double C;

@@ -335,34 +335,38 @@ __device__ __noinline__ void inner_rows(const InstDesc& I, int64_t n0, int h, fl
 // of the skew ring.
 
 // a lane's prefetched operands of one step: the delay value (row n-D, column q) and
-// the source tables at i = n-1-q
+// the source tables at i = n-1-q (zero-padded: 0 out of the light cone)
 struct Pre {
   float2 d, e, f;
 };
 
-// the constants of one lane's sweep
+// the constants of one lane's sweep (what only the edges use is read from I there)
 struct SweepC {
   const InstDesc* I;
   float2* skew;
-  const float2* rowD_in;   // inner ring row n-D (columns < D)
   const float2* __restrict__ detab32;
   const float2* __restrict__ phitab32;
-  float2* lo_row;
-  float2* snap;
   Hand* hand_out;          // queue to the warp below (lane 31), or null
   int R, n, nslot, sD, lane, D, nx, ncols, rd;
-  bool row_on, useD, is_last;
+  bool row_on, useD, is_last, snap;
   float2 R1, R2, d1, c2, c3, d1l, c2l, c3l;  // c3, c3l: 0 for rows without the delay square (n <= D)
 };
+__device__ __forceinline__ float2* snap_row(const InstDesc& I, int n) {
+  return I.snaps + (int64_t)(n / (I.tstep + 1)) * I.nx;
+}
 
 // its running state
 struct SweepS {
   float2 y, a_hi, a_lo, o_hi, o_lo, o_hn, dprev;
-  float nacc;
-  double dacc;
-  int dout;  // d-row (mod rd) of this step's outputs
-  int dpre;  // d-row (mod rd) of the delay value kPre steps ahead
+  float nsum, ncomp;       // the row's norm so far: Kahan sum over its columns in order
+  int dout;                // d-row (mod rd) of this step's outputs
+  int dpre;                // d-row (mod rd) of the delay value kPre steps ahead
   Pre pq[kPre];
+  // fast path (no wrap of the d-rows in the group): the same as pointers
+  float2* pout;
+  const float2* pdel;
+  const float2* pe;
+  const float2* pf;
 };
 
 __device__ __forceinline__ Pre sweep_fetch(const SweepC& c, int k, int dpre) {
@@ -371,58 +375,104 @@ __device__ __forceinline__ Pre sweep_fetch(const SweepC& c, int k, int dpre) {
   const float2 z = f2(0.f, 0.f);
   if (!c.useD) v.d = z;
   else if (q >= c.D) v.d = c.skew[(int64_t)dpre * c.R + c.sD];
-  else v.d = (q >= 0) ? c.rowD_in[q] : z;
-  // i < 0 (outside the light cone) and i - D < 0 read the tables' zero entry at -1
-  const int i = c.n - 1 - q, ip = i - c.D;
-  v.e = c.detab32[i < -1 ? -1 : i];
-  v.f = c.phitab32[ip < -1 ? -1 : ip];
+  else v.d = (q >= 0) ? c.I->ring[(int64_t)c.sD * c.I->stride + q] : z;  // inner ring, row n-D
+  const int i = c.n - 1 - q;
+  v.e = c.detab32[i];
+  v.f = c.phitab32[i - c.D];
   return v;
 }
 
-// one step.  FAST: every lane of the warp is marching a column of x > 3a (j >= 2D)
-// other than the last one
-template <bool FAST, int QI>
-__device__ __forceinline__ void sweep_step(const SweepC& c, SweepS& st, int k, float2 b_hi, float2 b_lo, float2 hp) {
+// the update of one column from S's parts: common to both steps
+__device__ __forceinline__ void sweep_core(const SweepC& c, SweepS& st, float2 hn, float2 b_hi, float2 hp, float2 S,
+                                           float2 L, float2& sv, float2& e) {
+  // b (row n-1, column j) and the delay pair of row n-D-1 from the lane above, and
+  // y (row n, column j-1), enter last: c2 (b + y) + c3 hp
+  S = add(S, st.a_lo);
+  const float2 t = add(b_hi, st.y);
+  S = fmac(c.c2, t, S);
+  S = fmac(c.c3, hp, S);
+  L = fmac(c.c3l, hp, L);
+  L = fmac(c.c2l, t, L);
+  S = add(S, L);
+  two_sum(st.a_hi.x, S.x, sv.x, e.x);
+  two_sum(st.a_hi.y, S.y, sv.y, e.y);
+}
+
+__device__ __forceinline__ void norm_add(SweepS& st, float x) {  // Kahan
+  const float yk = x - st.ncomp;
+  const float tk = st.nsum + yk;
+  st.ncomp = (tk - st.nsum) - yk;
+  st.nsum = tk;
+}
+
+// a step where every lane marches a column of x > 3a (j >= 2D) other than the last,
+// D >= 32 and no d-row wraps: operands by pointer, no tests
+template <int QI>
+__device__ __forceinline__ void sweep_step_fast(const SweepC& c, SweepS& st, int k, float2 b_hi, float2 b_lo,
+                                                float2 hp) {
+  const Pre pv = st.pq[QI];
+  const float2 hn = add(st.dprev, pv.d);
+  // the terms known before the lane above delivers row n-1: a (row n-1, column j-1),
+  // the delay pair of row n-D, the sources, a's remainder
+  float2 S = mulc(c.d1, st.a_hi);
+  float2 L = mulc(c.d1l, st.a_hi);
+  S = fmac(c.c3, hn, S);
+  L = fmac(c.c3l, hn, L);
+  S = fmac(c.R1, pv.e, S);
+  S = fmac(c.R2, pv.f, S);
+  float2 sv, e;
+  sweep_core(c, st, hn, b_hi, hp, S, L, sv, e);
+  *st.pout = sv;
+  st.pout += c.R;
   const int q = k - c.lane;
-  const bool act = FAST || (c.row_on && (unsigned)q < (unsigned)c.ncols);
+  if (c.is_last) c.I->lo_row[c.D + q] = e;
+  if (c.hand_out) c.hand_out[q & (kHandQ - 1)] = Hand{sv, e, hn};
+  norm_add(st, fmaf(sv.x, sv.x, sv.y * sv.y));
+  st.o_hi = sv;
+  st.o_lo = e;
+  st.o_hn = hn;
+  st.y = sv;
+  st.a_hi = b_hi;
+  st.a_lo = b_lo;
+  st.dprev = pv.d;
+  // the operands kPre steps ahead
+  Pre nv;
+  nv.d = c.useD ? *st.pdel : f2(0.f, 0.f);
+  nv.e = *st.pe;
+  nv.f = *st.pf;
+  st.pq[QI] = nv;
+  st.pdel += c.R;
+  --st.pe;
+  --st.pf;
+}
+
+// any other step (pipeline edges, a < x <= 3a, the last column, D < 32, d-row wraps)
+template <int QI>
+__device__ __forceinline__ void sweep_step_gen(const SweepC& c, SweepS& st, int k, float2 b_hi, float2 b_lo, float2 hp) {
+  const int q = k - c.lane;
+  const bool act = c.row_on && (unsigned)q < (unsigned)c.ncols;
   const int j = c.D + q;
   const Pre pv = st.pq[QI];
   const float2 hn = add(st.dprev, pv.d);
   float2 S = mulc(c.d1, st.a_hi);
-  S = fmac(c.c2, b_hi, S);
-  float2 L = fmac(c.c2l, b_hi, mulc(c.d1l, st.a_hi));
-  const float2 sq = add(hn, hp);
-  S = fmac(c.c3, sq, S);
-  L = fmac(c.c3l, sq, L);
-  S = add(S, L);
-  if (FAST || j >= 2 * c.D) {
+  float2 L = mulc(c.d1l, st.a_hi);
+  S = fmac(c.c3, hn, S);
+  L = fmac(c.c3l, hn, L);
+  if (j >= 2 * c.D) {
     S = fmac(c.R1, pv.e, S);
     S = fmac(c.R2, pv.f, S);
   } else if (act) {
     S = general_extra32(*c.I, c.n, c.nslot, j, c.R2, S);
   }
-  S = add(S, st.a_lo);
-  S = fmac(c.c2l, st.y, fmac(c.c2, st.y, S));
   float2 sv, e;
-  two_sum(st.a_hi.x, S.x, sv.x, e.x);
-  two_sum(st.a_hi.y, S.y, sv.y, e.y);
+  sweep_core(c, st, hn, b_hi, hp, S, L, sv, e);
   if (act) {
     c.skew[(int64_t)st.dout * c.R + c.nslot] = sv;
-    if (c.snap) c.snap[j] = sv;
-    if (c.is_last) c.lo_row[j] = e;
+    if (c.snap) snap_row(*c.I, c.n)[j] = sv;
+    if (c.is_last) c.I->lo_row[j] = e;
     if (c.hand_out) c.hand_out[q & (kHandQ - 1)] = Hand{sv, e, hn};
-    if (FAST) {
-      st.nacc = fmaf(sv.x, sv.x, st.nacc);
-      st.nacc = fmaf(sv.y, sv.y, st.nacc);
-    } else {
-      const float wt = (j == c.nx - 1) ? 0.5f : 1.0f;
-      st.nacc = fmaf(wt * sv.x, sv.x, st.nacc);
-      st.nacc = fmaf(wt * sv.y, sv.y, st.nacc);
-    }
-    if ((q & 15) == 15) {  // FP32 sums of 16 columns, FP64 across them
-      st.dacc += (double)st.nacc;
-      st.nacc = 0.f;
-    }
+    const float wt = (j == c.nx - 1) ? 0.5f : 1.0f;
+    norm_add(st, wt * fmaf(sv.x, sv.x, sv.y * sv.y));
     st.o_hi = sv;
     st.o_lo = e;
     st.o_hn = hn;
@@ -441,6 +491,36 @@ __device__ __forceinline__ void sweep_step(const SweepC& c, SweepS& st, int k, f
 __device__ __forceinline__ const float2* ring_at(const InstDesc& I, int r, int col) {
   if (col < I.D) return I.ring + (int64_t)(r % I.R) * I.stride + col;
   return I.skew + (int64_t)((r + col - I.D) % (int)I.rd) * I.R + (r % I.R);
+}
+
+// warp 0: issue the cp.async copies of chunk ch of the previous band's last row np
+// (value, remainder) and of its delay row np-D into buffer ch & 1, after waiting
+// (bounded, when wait_prev) until that band has done the chunk after it
+__device__ __noinline__ void stage_chunk(const InstDesc& I, int ch, int np, int ncols, bool wait_prev,
+                                         const unsigned long long* prev_word, unsigned long long tag_prev,
+                                         SyncWords* sync, float2 (*s_pv_hi)[kChunk], float2 (*s_pv_lo)[kChunk],
+                                         float2 (*s_pv_d)[kChunk + 1]) {
+  const int lane = threadIdx.x & 31, D = I.D;
+  if (wait_prev && lane == 0) {
+    const int cols = (ch + 1) * kChunk;
+    wait_ge_global(prev_word, tag_prev + (unsigned long long)(cols < ncols ? cols : ncols), I.spin, sync, np + 1);
+  }
+  __syncwarp();
+  const float2 z = f2(0.f, 0.f);
+  const bool pd = (np >= D);
+  const int b = ch & 1, q = ch * kChunk + lane;
+  if (q < ncols) {
+    cp_async8(&s_pv_hi[b][lane], ring_at(I, np, D + q));
+    cp_async8(&s_pv_lo[b][lane], I.lo_row + D + q);
+    if (pd) cp_async8(&s_pv_d[b][lane + 1], ring_at(I, np - D, q));
+    else s_pv_d[b][lane + 1] = z;
+  }
+  if (lane == 0 && ch * kChunk < ncols) {  // the delay value left of the chunk's first column
+    if (!pd) s_pv_d[b][0] = z;
+    else if (ch == 0) s_pv_d[b][0] = psi_left32(I, np - D, -(D >> 1));
+    else cp_async8(&s_pv_d[b][0], ring_at(I, np - D, ch * kChunk - 1));
+  }
+  cp_async_commit();
 }
 
 // rows n0 .. n0+h-1 (row n0+tid on thread tid), columns D .. nx-1.  wait_prev:
@@ -465,12 +545,14 @@ __device__ __noinline__ void sweep(const InstDesc& I, int n0, int h, bool wait_p
   const bool is_last = (tid == t_last);
   const bool last_warp = (warp == (t_last >> 5));
   const unsigned long long tag = (unsigned long long)n0 << 32;
-
-  double inner = 0.0;
-  if (row_on)
+  auto inner_norm = [&]() {  // the row's inner columns (the inner pass's warp sums)
+    double t = 0.0;
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) inner += (double)s_wn[w][tid];
+    for (int w = 0; w < kWarps; ++w) t += (double)s_wn[w][tid];
+    return t;
+  };
   if (ncols <= 0) {
+    const double inner = row_on ? inner_norm() : 0.0;
     if (row_on) I.norms[n] = I.delta * (inner + I.bnorm[n]);
     if (last_warp) {
       __syncwarp();
@@ -484,7 +566,6 @@ __device__ __noinline__ void sweep(const InstDesc& I, int n0, int h, bool wait_p
   c.skew = I.skew;
   c.detab32 = I.detab32;
   c.phitab32 = I.phitab32;
-  c.lo_row = I.lo_row;
   c.R = R;
   c.n = n;
   c.nslot = n % R;
@@ -499,10 +580,9 @@ __device__ __noinline__ void sweep(const InstDesc& I, int n0, int h, bool wait_p
   c.useD = hasD && D >= kPre;  // a delay value kPre steps ahead is not yet written when D < kPre
   const bool sqon = row_on && n >= D + 1;
   c.is_last = is_last;
-  c.rowD_in = I.ring + (int64_t)(hasD ? c.sD : 0) * I.stride;
   c.R1 = I.rowscal32[2 * n];
   c.R2 = I.rowscal32[2 * n + 1];
-  c.snap = (row_on && I.tstep >= 0 && n % (I.tstep + 1) == 0) ? I.snaps + (int64_t)(n / (I.tstep + 1)) * nx : nullptr;
+  c.snap = row_on && I.tstep >= 0 && n % (I.tstep + 1) == 0;
   c.hand_out = (lane == 31 && next_on) ? s_hand[warp] : nullptr;
   c.d1 = I.d1;
   c.c2 = I.c2;
@@ -511,6 +591,8 @@ __device__ __noinline__ void sweep(const InstDesc& I, int n0, int h, bool wait_p
   c.c2l = I.c2lo;
   c.c3l = sqon ? I.c3lo : z;
   const bool direct_d = hasD && D < kPre;
+  // a warp holding a snapshot row takes the general step throughout
+  const bool warp_snap = __any_sync(0xffffffffu, c.snap);
 
   // state at column D: y = psi[n][D-1] (inner pass), a = psi[n-1][D-1] + its remainder,
   // the delay value left of storage column 0 (x <= -a)
@@ -521,8 +603,8 @@ __device__ __noinline__ void sweep(const InstDesc& I, int n0, int h, bool wait_p
   st.a_lo = row_on ? I.lo_edge[n - 1] : z;
   st.dprev = hasD ? psi_left32(I, n - D, -Dh) : z;
   st.o_hi = st.o_lo = st.o_hn = z;
-  st.nacc = 0.f;
-  st.dacc = 0.0;
+  st.nsum = 0.f;
+  st.ncomp = 0.f;
   st.dout = ((nw % c.rd) + c.rd) % c.rd;
   st.dpre = (((nw - 2 * D) % c.rd) + c.rd) % c.rd;
 #pragma unroll
@@ -531,35 +613,11 @@ __device__ __noinline__ void sweep(const InstDesc& I, int n0, int h, bool wait_p
     st.dpre = (st.dpre + 1 == c.rd) ? 0 : st.dpre + 1;
   }
 
-  // warp 0: the previous band's last row n0-1 (value, remainder) and its delay row
-  // n0-1-D, copied 32 columns at a time into shared memory (cp.async, one chunk ahead)
-  const int np = n0 - 1;
-  const bool pd = (np >= D);
-  auto stage = [&](int ch) {  // warp 0: issue the copies of chunk ch into buffer ch & 1
-    const int b = ch & 1, q = ch * kChunk + lane;
-    if (q < ncols) {
-      cp_async8(&s_pv_hi[b][lane], ring_at(I, np, D + q));
-      cp_async8(&s_pv_lo[b][lane], I.lo_row + D + q);
-      if (pd) cp_async8(&s_pv_d[b][lane + 1], ring_at(I, np - D, q));
-      else s_pv_d[b][lane + 1] = z;
-    }
-    if (lane == 0 && ch * kChunk < ncols) {  // the delay value left of the chunk's first column
-      if (!pd) s_pv_d[b][0] = z;
-      else if (ch == 0) s_pv_d[b][0] = psi_left32(I, np - D, -Dh);
-      else cp_async8(&s_pv_d[b][0], ring_at(I, np - D, ch * kChunk - 1));
-    }
-    cp_async_commit();
-  };
-  auto prev_wait = [&](int cols) {  // warp 0: band c-1's last row has done `cols` columns
-    if (wait_prev && lane == 0)
-      wait_ge_global(prev_word, tag - ((unsigned long long)kBand << 32) + (unsigned long long)(cols < ncols ? cols : ncols),
-                     spin, sync, n0);
-    __syncwarp();
-  };
+  // warp 0: the previous band's last row through shared memory, a chunk ahead
   if (warp == 0) {
-    prev_wait(2 * kChunk);
-    stage(0);
-    stage(1);
+    const unsigned long long tag_prev = (unsigned long long)(n0 - kBand) << 32;
+    stage_chunk(I, 0, n0 - 1, ncols, wait_prev, prev_word, tag_prev, sync, s_pv_hi, s_pv_lo, s_pv_d);
+    stage_chunk(I, 1, n0 - 1, ncols, wait_prev, prev_word, tag_prev, sync, s_pv_hi, s_pv_lo, s_pv_d);
     cp_async_wait1();  // chunk 0 is in shared memory
     __syncwarp();
   }
@@ -571,15 +629,14 @@ __device__ __noinline__ void sweep(const InstDesc& I, int n0, int h, bool wait_p
     // ---- bookkeeping every kGrp steps
     __syncwarp();
     if (warp == 0 && kb > 0 && (kb % kChunk) == 0) {  // chunk ch+1 on its way, chunk ch in place
-      const int ch = kb / kChunk;
-      prev_wait((ch + 2) * kChunk);
-      stage(ch + 1);
+      stage_chunk(I, kb / kChunk + 1, n0 - 1, ncols, wait_prev, prev_word, (unsigned long long)(n0 - kBand) << 32,
+                  sync, s_pv_hi, s_pv_lo, s_pv_d);
       cp_async_wait1();
       __syncwarp();
     }
     if (last_warp && (kb % kChunk) == 0 && is_last) {  // progress of the band's last row, for band c+1
       const int done = kb - lane;
-      st_release_u64(my_word, tag + (unsigned long long)(done < 0 ? 0 : (done > ncols ? ncols : done)));
+      st_release_u64(my_word, ((unsigned long long)n0 << 32) + (unsigned long long)(done < 0 ? 0 : (done > ncols ? ncols : done)));
     }
     if (warp > 0 && lane == 0) {  // consumer of the warp above
       __threadfence_block();
@@ -596,36 +653,63 @@ __device__ __noinline__ void sweep(const InstDesc& I, int n0, int h, bool wait_p
     }
     __syncwarp();
 
-    const bool fast = warp_full && kb >= kfast0 && kb + kGrp <= kfast1;
-    for (int uu = 0; uu < kGrp; uu += kPre) {
+    const bool fast = warp_full && !warp_snap && D >= 32 && kb >= kfast0 && kb + kGrp <= kfast1 &&
+                      st.dout + kGrp < c.rd && st.dpre + kGrp < c.rd;
+    if (fast) {
+      st.pout = c.skew + (int64_t)st.dout * R + c.nslot;
+      st.pdel = c.skew + (int64_t)st.dpre * R + c.sD;
+      const int i = n - 1 - (kb + kPre - lane);  // the tables at step kb + kPre
+      st.pe = c.detab32 + i;
+      st.pf = c.phitab32 + (i - D);
+      for (int uu = 0; uu < kGrp; uu += kPre) {
 #pragma unroll
-      for (int u = 0; u < kPre; ++u) {
-        const int k = kb + uu + u;
-        // row n-1 at this step's column, from the lane above (its previous step)
-        float2 b_hi = shfl_up2(st.o_hi, 1), b_lo = shfl_up2(st.o_lo, 1), hp = shfl_up2(st.o_hn, 1);
-        if (lane == 0 && k < ncols) {
-          if (warp > 0) {
-            const Hand hd = s_hand[warp - 1][k & (kHandQ - 1)];
-            b_hi = hd.hi;
-            b_lo = hd.lo;
-            hp = hd.hn;
-          } else {
-            const int b = (k / kChunk) & 1, x = k % kChunk;
-            b_hi = s_pv_hi[b][x];
-            b_lo = s_pv_lo[b][x];
-            hp = add(s_pv_d[b][x], s_pv_d[b][x + 1]);
+        for (int u = 0; u < kPre; ++u) {
+          const int k = kb + uu + u;
+          float2 b_hi = shfl_up2(st.o_hi, 1), b_lo = shfl_up2(st.o_lo, 1), hp = shfl_up2(st.o_hn, 1);
+          if (lane == 0) {
+            if (warp > 0) {
+              const Hand hd = s_hand[warp - 1][k & (kHandQ - 1)];
+              b_hi = hd.hi;
+              b_lo = hd.lo;
+              hp = hd.hn;
+            } else {
+              const int bb = (k / kChunk) & 1, x = k % kChunk;
+              b_hi = s_pv_hi[bb][x];
+              b_lo = s_pv_lo[bb][x];
+              hp = add(s_pv_d[bb][x], s_pv_d[bb][x + 1]);
+            }
           }
+          if (u == 0) sweep_step_fast<0>(c, st, k, b_hi, b_lo, hp);
+          else sweep_step_fast<1>(c, st, k, b_hi, b_lo, hp);
         }
-        if (direct_d) {  // D < kPre: the delay value is read at its step
-          const int q = k - lane;
-          st.pq[u].d = ((unsigned)q < (unsigned)ncols) ? *ring_at(I, n - D, q) : z;
-        }
-        if (fast) {
-          if (u == 0) sweep_step<true, 0>(c, st, k, b_hi, b_lo, hp);
-          else sweep_step<true, 1>(c, st, k, b_hi, b_lo, hp);
-        } else {
-          if (u == 0) sweep_step<false, 0>(c, st, k, b_hi, b_lo, hp);
-          else sweep_step<false, 1>(c, st, k, b_hi, b_lo, hp);
+      }
+      st.dout += kGrp;
+      st.dpre += kGrp;
+    } else {
+      for (int uu = 0; uu < kGrp; uu += kPre) {
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+          const int k = kb + uu + u;
+          float2 b_hi = shfl_up2(st.o_hi, 1), b_lo = shfl_up2(st.o_lo, 1), hp = shfl_up2(st.o_hn, 1);
+          if (lane == 0 && k < ncols) {
+            if (warp > 0) {
+              const Hand hd = s_hand[warp - 1][k & (kHandQ - 1)];
+              b_hi = hd.hi;
+              b_lo = hd.lo;
+              hp = hd.hn;
+            } else {
+              const int bb = (k / kChunk) & 1, x = k % kChunk;
+              b_hi = s_pv_hi[bb][x];
+              b_lo = s_pv_lo[bb][x];
+              hp = add(s_pv_d[bb][x], s_pv_d[bb][x + 1]);
+            }
+          }
+          if (direct_d) {  // D < kPre: the delay value is read at its step
+            const int q = k - lane;
+            st.pq[u].d = ((unsigned)q < (unsigned)ncols) ? *ring_at(I, n - D, q) : z;
+          }
+          if (u == 0) sweep_step_gen<0>(c, st, k, b_hi, b_lo, hp);
+          else sweep_step_gen<1>(c, st, k, b_hi, b_lo, hp);
         }
       }
     }
@@ -635,8 +719,8 @@ __device__ __noinline__ void sweep(const InstDesc& I, int n0, int h, bool wait_p
     __threadfence_block();
     s_prod[warp] = ncols;
   }
-  if (is_last) st_release_u64(my_word, tag + (unsigned long long)ncols);
-  if (row_on) I.norms[n] = I.delta * (inner + (st.dacc + (double)st.nacc) + I.bnorm[n]);
+  if (is_last) st_release_u64(my_word, ((unsigned long long)n0 << 32) + (unsigned long long)ncols);
+  if (row_on) I.norms[n] = I.delta * (inner_norm() + ((double)st.nsum - (double)st.ncomp) + I.bnorm[n]);
 }
 
 // row r of an instance between its rings and a row-major buffer (see RowMap)
