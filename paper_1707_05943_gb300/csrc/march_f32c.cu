@@ -64,6 +64,18 @@ struct Hand {
 
 }  // namespace
 
+// the march kernel's shared memory, at namespace scope so that every helper addresses
+// it as shared memory (a pointer parameter would make each access a generic one)
+__shared__ Hand s_queue[kWarps][kHandQ];  // lane 0's input of warp w: warp w-1's last row (w > 0)
+                                          // or the previous band's last row (w = 0)
+__shared__ int s_prod[kWarps], s_cons[kWarps];
+__shared__ float2 s_pv_hi[2][kChunk], s_pv_lo[2][kChunk], s_pv_d[2][kChunk + 1];
+__shared__ float s_wn[kWarps][kBand];
+__shared__ float2 s_scP[kWarps], s_scY[kWarps];
+__shared__ float2 s_ylast;
+__shared__ int s_item;
+__shared__ __align__(16) InstDesc s_I;  // the instance's descriptor: no global store can alias it
+
 __device__ __forceinline__ float2 f2(float r, float i) { return make_float2(r, i); }
 __device__ __forceinline__ float2 add(float2 a, float2 b) { return f2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 sub(float2 a, float2 b) { return f2(a.x - b.x, a.y - b.y); }
@@ -155,7 +167,8 @@ __device__ __forceinline__ float2 rhs_inner32(const InstDesc& I, int64_t n, int 
 // the mirror terms of a column D <= j < 2D (a < x <= 3a) of row n, added to S: the
 // bar of row r2 = n-j-1 lies at x <= -a; the bar of row r3 = r2 + D reads ring
 // columns 2D-j-2, 2D-j-1 (inner columns) and the boundary tables
-__device__ __noinline__ float2 general_extra32(const InstDesc& I, int n, int nslot, int j, float2 R2, float2 S) {
+__device__ __noinline__ float2 general_extra32(int n, int nslot, int j, float2 R2, float2 S) {
+  const InstDesc& I = s_I;
   const int D = I.D, Dh = D >> 1;
   const int m = j - Dh + 1;
   const int r2 = n - j - 1, r3 = r2 + D;
@@ -229,8 +242,8 @@ __device__ __forceinline__ void wait_ge_shared(volatile int* p, int target, long
 
 // ---------------------------------------------------------------- inner columns
 // rows n0 .. n0+h-1, columns 0 .. D-1, row by row (every thread of the CTA)
-__device__ __noinline__ void inner_rows(const InstDesc& I, int64_t n0, int h, float (*s_wn)[kBand],
-                                           float2* s_scP, float2* s_scY, float2* s_ylast) {
+__device__ __noinline__ void inner_rows(int64_t n0, int h) {
+  const InstDesc& I = s_I;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int D = I.D;
   for (int r = 0; r < h; ++r) {
@@ -317,9 +330,9 @@ __device__ __noinline__ void inner_rows(const InstDesc& I, int64_t n0, int h, fl
           y = sv;
         }
       }
-      if (j0 < j1 && j1 == c0 + cw) *s_ylast = y;  // carry into the next pass
+      if (j0 < j1 && j1 == c0 + cw) s_ylast = y;  // carry into the next pass
       __syncthreads();  // row n's inner columns are stored; the scan buffers are free
-      ycar = *s_ylast;
+      ycar = s_ylast;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nacc += __shfl_down_sync(0xffffffffu, nacc, o);
@@ -342,13 +355,11 @@ struct Pre {
 
 // the constants of one lane's sweep (what only the edges use is read from I there)
 struct SweepC {
-  const InstDesc* I;
   float2* skew;
   const float2* __restrict__ detab32;
   const float2* __restrict__ phitab32;
-  Hand* hand_out;          // queue to the warp below (lane 31), or null
-  int R, n, nslot, sD, lane, D, nx, ncols, rd;
-  bool row_on, useD, is_last, snap;
+  int R, n, nslot, sD, lane, warp, D, nx, ncols, rd;
+  bool row_on, useD, is_last, snap, hand_out;  // hand_out: lane 31 feeding the warp below
   float2 R1, R2, d1, c2, c3, d1l, c2l, c3l;  // c3, c3l: 0 for rows without the delay square (n <= D)
 };
 __device__ __forceinline__ float2* snap_row(const InstDesc& I, int n) {
@@ -375,7 +386,7 @@ __device__ __forceinline__ Pre sweep_fetch(const SweepC& c, int k, int dpre) {
   const float2 z = f2(0.f, 0.f);
   if (!c.useD) v.d = z;
   else if (q >= c.D) v.d = c.skew[(int64_t)dpre * c.R + c.sD];
-  else v.d = (q >= 0) ? c.I->ring[(int64_t)c.sD * c.I->stride + q] : z;  // inner ring, row n-D
+  else v.d = (q >= 0) ? s_I.ring[(int64_t)c.sD * s_I.stride + q] : z;  // inner ring, row n-D
   const int i = c.n - 1 - q;
   v.e = c.detab32[i];
   v.f = c.phitab32[i - c.D];
@@ -425,8 +436,8 @@ __device__ __forceinline__ void sweep_step_fast(const SweepC& c, SweepS& st, int
   *st.pout = sv;
   st.pout += c.R;
   const int q = k - c.lane;
-  if (c.is_last) c.I->lo_row[c.D + q] = e;
-  if (c.hand_out) c.hand_out[q & (kHandQ - 1)] = Hand{sv, e, hn};
+  if (c.is_last) s_I.lo_row[c.D + q] = e;
+  if (c.hand_out) s_queue[c.warp + 1][q & (kHandQ - 1)] = Hand{sv, e, hn};
   norm_add(st, fmaf(sv.x, sv.x, sv.y * sv.y));
   st.o_hi = sv;
   st.o_lo = e;
@@ -462,15 +473,15 @@ __device__ __forceinline__ void sweep_step_gen(const SweepC& c, SweepS& st, int 
     S = fmac(c.R1, pv.e, S);
     S = fmac(c.R2, pv.f, S);
   } else if (act) {
-    S = general_extra32(*c.I, c.n, c.nslot, j, c.R2, S);
+    S = general_extra32(c.n, c.nslot, j, c.R2, S);
   }
   float2 sv, e;
   sweep_core(c, st, hn, b_hi, hp, S, L, sv, e);
   if (act) {
     c.skew[(int64_t)st.dout * c.R + c.nslot] = sv;
-    if (c.snap) snap_row(*c.I, c.n)[j] = sv;
-    if (c.is_last) c.I->lo_row[j] = e;
-    if (c.hand_out) c.hand_out[q & (kHandQ - 1)] = Hand{sv, e, hn};
+    if (c.snap) snap_row(s_I, c.n)[j] = sv;
+    if (c.is_last) s_I.lo_row[j] = e;
+    if (c.hand_out) s_queue[c.warp + 1][q & (kHandQ - 1)] = Hand{sv, e, hn};
     const float wt = (j == c.nx - 1) ? 0.5f : 1.0f;
     norm_add(st, wt * fmaf(sv.x, sv.x, sv.y * sv.y));
     st.o_hi = sv;
@@ -496,10 +507,9 @@ __device__ __forceinline__ const float2* ring_at(const InstDesc& I, int r, int c
 // warp 0: issue the cp.async copies of chunk ch of the previous band's last row np
 // (value, remainder) and of its delay row np-D into buffer ch & 1, after waiting
 // (bounded, when wait_prev) until that band has done the chunk after it
-__device__ __noinline__ void stage_chunk(const InstDesc& I, int ch, int np, int ncols, bool wait_prev,
-                                         const unsigned long long* prev_word, unsigned long long tag_prev,
-                                         SyncWords* sync, float2 (*s_pv_hi)[kChunk], float2 (*s_pv_lo)[kChunk],
-                                         float2 (*s_pv_d)[kChunk + 1]) {
+__device__ __noinline__ void stage_chunk(int ch, int np, int ncols, bool wait_prev, const unsigned long long* prev_word,
+                                         unsigned long long tag_prev, SyncWords* sync) {
+  const InstDesc& I = s_I;
   const int lane = threadIdx.x & 31, D = I.D;
   if (wait_prev && lane == 0) {
     const int cols = (ch + 1) * kChunk;
@@ -523,13 +533,20 @@ __device__ __noinline__ void stage_chunk(const InstDesc& I, int ch, int np, int 
   cp_async_commit();
 }
 
+// warp 0: chunk ch (in shared memory) into its input queue, in the format of the
+// queues between warps: entry q & 63 = (value, remainder, delay pair sum) of column q
+__device__ __forceinline__ void chunk_to_queue(int ch) {
+  const int lane = threadIdx.x & 31, b = ch & 1;
+  s_queue[0][(ch * kChunk + lane) & (kHandQ - 1)] =
+      Hand{s_pv_hi[b][lane], s_pv_lo[b][lane], add(s_pv_d[b][lane], s_pv_d[b][lane + 1])};
+  __syncwarp();
+}
+
 // rows n0 .. n0+h-1 (row n0+tid on thread tid), columns D .. nx-1.  wait_prev:
 // band c-1 (progress word prev_word, first row n0-256) is still being marched.
-__device__ __noinline__ void sweep(const InstDesc& I, int n0, int h, bool wait_prev,
-                                   const unsigned long long* prev_word, unsigned long long* my_word,
-                                   SyncWords* sync, Hand (*s_hand)[kHandQ], volatile int* s_prod,
-                                   volatile int* s_cons, float2 (*s_pv_hi)[kChunk], float2 (*s_pv_lo)[kChunk],
-                                   float2 (*s_pv_d)[kChunk + 1], const float (*s_wn)[kBand]) {
+__device__ __noinline__ void sweep(int n0, int h, bool wait_prev, const unsigned long long* prev_word,
+                                   unsigned long long* my_word, SyncWords* sync) {
+  const InstDesc& I = s_I;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (warp * 32 >= h) return;
   const float2 z = f2(0.f, 0.f);
@@ -562,7 +579,6 @@ __device__ __noinline__ void sweep(const InstDesc& I, int n0, int h, bool wait_p
   }
 
   SweepC c;
-  c.I = &I;
   c.skew = I.skew;
   c.detab32 = I.detab32;
   c.phitab32 = I.phitab32;
@@ -583,7 +599,8 @@ __device__ __noinline__ void sweep(const InstDesc& I, int n0, int h, bool wait_p
   c.R1 = I.rowscal32[2 * n];
   c.R2 = I.rowscal32[2 * n + 1];
   c.snap = row_on && I.tstep >= 0 && n % (I.tstep + 1) == 0;
-  c.hand_out = (lane == 31 && next_on) ? s_hand[warp] : nullptr;
+  c.warp = warp;
+  c.hand_out = (lane == 31 && next_on);
   c.d1 = I.d1;
   c.c2 = I.c2;
   c.c3 = sqon ? I.c3 : z;
@@ -616,11 +633,13 @@ __device__ __noinline__ void sweep(const InstDesc& I, int n0, int h, bool wait_p
   // warp 0: the previous band's last row through shared memory, a chunk ahead
   if (warp == 0) {
     const unsigned long long tag_prev = (unsigned long long)(n0 - kBand) << 32;
-    stage_chunk(I, 0, n0 - 1, ncols, wait_prev, prev_word, tag_prev, sync, s_pv_hi, s_pv_lo, s_pv_d);
-    stage_chunk(I, 1, n0 - 1, ncols, wait_prev, prev_word, tag_prev, sync, s_pv_hi, s_pv_lo, s_pv_d);
+    stage_chunk(0, n0 - 1, ncols, wait_prev, prev_word, tag_prev, sync);
+    stage_chunk(1, n0 - 1, ncols, wait_prev, prev_word, tag_prev, sync);
     cp_async_wait1();  // chunk 0 is in shared memory
     __syncwarp();
+    chunk_to_queue(0);
   }
+
 
   // steps [kfast0, kfast1): every lane marching a column j >= 2D other than the last
   const int kfast0 = D + 31, kfast1 = ncols - 1;
@@ -629,10 +648,10 @@ __device__ __noinline__ void sweep(const InstDesc& I, int n0, int h, bool wait_p
     // ---- bookkeeping every kGrp steps
     __syncwarp();
     if (warp == 0 && kb > 0 && (kb % kChunk) == 0) {  // chunk ch+1 on its way, chunk ch in place
-      stage_chunk(I, kb / kChunk + 1, n0 - 1, ncols, wait_prev, prev_word, (unsigned long long)(n0 - kBand) << 32,
-                  sync, s_pv_hi, s_pv_lo, s_pv_d);
+      stage_chunk(kb / kChunk + 1, n0 - 1, ncols, wait_prev, prev_word, (unsigned long long)(n0 - kBand) << 32, sync);
       cp_async_wait1();
       __syncwarp();
+      chunk_to_queue(kb / kChunk);
     }
     if (last_warp && (kb % kChunk) == 0 && is_last) {  // progress of the band's last row, for band c+1
       const int done = kb - lane;
@@ -640,16 +659,16 @@ __device__ __noinline__ void sweep(const InstDesc& I, int n0, int h, bool wait_p
     }
     if (warp > 0 && lane == 0) {  // consumer of the warp above
       __threadfence_block();
-      s_cons[warp] = (kb < ncols) ? kb : ncols;
+      ((volatile int*)s_cons)[warp] = (kb < ncols) ? kb : ncols;
       const int need = (kb + 2 * kGrp < ncols) ? kb + 2 * kGrp : ncols;
-      wait_ge_shared(s_prod + warp - 1, need, spin, sync, n0);
+      wait_ge_shared((volatile int*)s_prod + warp - 1, need, spin, sync, n0);
     }
     if (next_on && lane == 31) {  // producer for the warp below
       __threadfence_block();
       const int done = kb - 31;
-      s_prod[warp] = (done < 0) ? 0 : (done > ncols ? ncols : done);
+      ((volatile int*)s_prod)[warp] = (done < 0) ? 0 : (done > ncols ? ncols : done);
       const int need = kb + kGrp - 32 - kHandQ + 1;  // the entries this group overwrites were consumed
-      if (need > 0) wait_ge_shared(s_cons + warp + 1, (need < ncols) ? need : ncols, spin, sync, n0);
+      if (need > 0) wait_ge_shared((volatile int*)s_cons + warp + 1, (need < ncols) ? need : ncols, spin, sync, n0);
     }
     __syncwarp();
 
@@ -665,19 +684,14 @@ __device__ __noinline__ void sweep(const InstDesc& I, int n0, int h, bool wait_p
 #pragma unroll
         for (int u = 0; u < kPre; ++u) {
           const int k = kb + uu + u;
+          // row n-1 at this step's column: from the lane above (its previous step), lane 0
+          // from its queue (every lane reads the same entry: a broadcast, no branch)
           float2 b_hi = shfl_up2(st.o_hi, 1), b_lo = shfl_up2(st.o_lo, 1), hp = shfl_up2(st.o_hn, 1);
+          const Hand hd = s_queue[warp][k & (kHandQ - 1)];
           if (lane == 0) {
-            if (warp > 0) {
-              const Hand hd = s_hand[warp - 1][k & (kHandQ - 1)];
-              b_hi = hd.hi;
-              b_lo = hd.lo;
-              hp = hd.hn;
-            } else {
-              const int bb = (k / kChunk) & 1, x = k % kChunk;
-              b_hi = s_pv_hi[bb][x];
-              b_lo = s_pv_lo[bb][x];
-              hp = add(s_pv_d[bb][x], s_pv_d[bb][x + 1]);
-            }
+            b_hi = hd.hi;
+            b_lo = hd.lo;
+            hp = hd.hn;
           }
           if (u == 0) sweep_step_fast<0>(c, st, k, b_hi, b_lo, hp);
           else sweep_step_fast<1>(c, st, k, b_hi, b_lo, hp);
@@ -691,18 +705,11 @@ __device__ __noinline__ void sweep(const InstDesc& I, int n0, int h, bool wait_p
         for (int u = 0; u < kPre; ++u) {
           const int k = kb + uu + u;
           float2 b_hi = shfl_up2(st.o_hi, 1), b_lo = shfl_up2(st.o_lo, 1), hp = shfl_up2(st.o_hn, 1);
-          if (lane == 0 && k < ncols) {
-            if (warp > 0) {
-              const Hand hd = s_hand[warp - 1][k & (kHandQ - 1)];
-              b_hi = hd.hi;
-              b_lo = hd.lo;
-              hp = hd.hn;
-            } else {
-              const int bb = (k / kChunk) & 1, x = k % kChunk;
-              b_hi = s_pv_hi[bb][x];
-              b_lo = s_pv_lo[bb][x];
-              hp = add(s_pv_d[bb][x], s_pv_d[bb][x + 1]);
-            }
+          const Hand hd = s_queue[warp][k & (kHandQ - 1)];
+          if (lane == 0) {  // (an entry past the last column is stale; lane 0 is idle then)
+            b_hi = hd.hi;
+            b_lo = hd.lo;
+            hp = hd.hn;
           }
           if (direct_d) {  // D < kPre: the delay value is read at its step
             const int q = k - lane;
@@ -717,7 +724,7 @@ __device__ __noinline__ void sweep(const InstDesc& I, int n0, int h, bool wait_p
   __syncwarp();
   if (next_on && lane == 31) {
     __threadfence_block();
-    s_prod[warp] = ncols;
+    ((volatile int*)s_prod)[warp] = ncols;
   }
   if (is_last) st_release_u64(my_word, ((unsigned long long)n0 << 32) + (unsigned long long)ncols);
   if (row_on) I.norms[n] = I.delta * (inner_norm() + ((double)st.nsum - (double)st.ncomp) + I.bnorm[n]);
@@ -742,14 +749,6 @@ cudaError_t launch_row_move(const RowMap& m, int64_t r, float2* buf, int dir, cu
 __global__ void __launch_bounds__(kF32Threads, 2)
     k_march_f32c(const InstDesc* __restrict__ insts, const WorkItem* __restrict__ items, int nitems,
                  unsigned int* queue, SyncWords* sync) {
-  __shared__ Hand s_hand[kWarps - 1][kHandQ];
-  __shared__ int s_prod[kWarps], s_cons[kWarps];
-  __shared__ float2 s_pv_hi[2][kChunk], s_pv_lo[2][kChunk], s_pv_d[2][kChunk + 1];
-  __shared__ float s_wn[kWarps][kBand];
-  __shared__ float2 s_scP[kWarps], s_scY[kWarps];
-  __shared__ float2 s_ylast;
-  __shared__ int s_item;
-  __shared__ __align__(16) InstDesc s_I;  // the instance's descriptor: no global store can alias it
 
   const int tid = threadIdx.x;
   for (;;) {
@@ -783,11 +782,10 @@ __global__ void __launch_bounds__(kF32Threads, 2)
           s_prod[tid] = 0;
           s_cons[tid] = 0;
         }
-        inner_rows(I, n0, h, s_wn, s_scP, s_scY, &s_ylast);
+        inner_rows(n0, h);
         __syncthreads();
         if (tid == 0) st_release_u64(gdone, (unsigned long long)(n0 + h));
-        sweep(I, (int)n0, h, !first && g > 1, prog + (r + g - 1) % g, prog + r, sync, s_hand, s_prod, s_cons,
-              s_pv_hi, s_pv_lo, s_pv_d, s_wn);
+        sweep((int)n0, h, !first && g > 1, prog + (r + g - 1) % g, prog + r, sync);
       }
     }
     __syncthreads();  // s_item and s_I are read by every thread before they are rewritten
