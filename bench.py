@@ -190,10 +190,11 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "small", "batch", "precision", "surrogate"])
+    ap.add_argument("--workload", default="large",
+                    choices=["large", "small", "batch", "precision", "surrogate", "uniform"])
     ap.add_argument("--batch-n", type=int, default=256, help="instances of the seeded batch")
     ap.add_argument("--compare-f64", action="store_true", help="also march the batch in FP64, one plan each")
-    ap.add_argument("--no-autotune", action="store_true", help="batch: default cluster width and split weight")
+    ap.add_argument("--no-autotune", action="store_true", help="batch: default band streams per instance and stream share")
     ap.add_argument("--rows", type=int, default=0, help="march only this many rows (profiling)")
     ap.add_argument("--nx", type=int, default=0, help="march only this many columns (profiling)")
     ap.add_argument("--D", type=int, default=0, help="use this D at the same delta (profiling)")
@@ -210,7 +211,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
 
-    if args.workload in ("batch", "precision", "surrogate"):
+    if args.workload in ("batch", "precision", "surrogate", "uniform"):
         if args.impl == "reference":
             run_reference(args, W.PRECISION if args.workload != "batch" else W.batch(n=args.batch_n)[0])
         else:
@@ -442,8 +443,17 @@ def c64_variant(args, which, steps, warmup, peaks, src):
 
     from paper_1707_05943_gb300 import fdtd as F
     local = env_rank()[2]
-    ws_list = W.batch(n=args.batch_n) if which == "batch" else [W.PRECISION]
-    name = f"batch1707_n{len(ws_list)}" if which == "batch" else W.PRECISION.name
+    if which == "uniform":  # --batch-n copies of the precision physics at --nx x (--rows + 1), --D
+        nx, rows_u, D = args.nx or 4096, args.rows or 1024, args.D or 40
+        one = W.PRECISION.with_(nx=nx, nt=rows_u + 1, D=D, delta=W.PRECISION.delta, name="uniform")
+        ws_list = [one] * args.batch_n
+        name = f"uniform_n{args.batch_n}_nx{nx}_nt{rows_u + 1}_D{D}"
+    elif which == "batch":
+        ws_list = W.batch(n=args.batch_n)
+        name = f"batch1707_n{len(ws_list)}"
+    else:
+        ws_list = [W.PRECISION]
+        name = W.PRECISION.name
 
     def cfg(w, prec, tstep=-1, cluster_ctas=0, mid_weight=0):
         return F.Config(nx=w.nx, nt=w.nt, D=w.D, delta=w.delta, gamma=w.gamma, omega0=w.omega0, k=w.k,
@@ -453,7 +463,7 @@ def c64_variant(args, which, steps, warmup, peaks, src):
     knobs, tuned = {}, None
     if which == "batch" and not args.no_autotune:
         from paper_1707_05943_gb300 import autotune as A
-        ch = A.tune([cfg(w, F.F32_COMP) for w in ws_list], rows=256)
+        ch = A.tune([cfg(w, F.F32_COMP) for w in ws_list], rows=1024)
         knobs = {"cluster_ctas": ch.cluster_ctas, "mid_weight": ch.mid_weight}
         tuned = {"cluster_ctas": ch.cluster_ctas, "mid_weight": ch.mid_weight, "key": ch.key,
                  "estimated_march_ms": ch.table}
@@ -542,8 +552,7 @@ def c64_variant(args, which, steps, warmup, peaks, src):
            "config": {"workload": name, "instances": len(ws_list), "updates_per_step": updates,
                       "march": "CUDA graph of the persistent launches (fdtd_march_graph)",
                       "autotune": tuned,
-                      "l2": "inputs larger than L2 (rings of all instances "
-                            f"{sum((w.D + 2) * w.nx * 8 for w in ws_list) / 1e9:.1f} GB)"},
+                      "l2": f"inputs larger than L2 (plan workspace {nbytes.value / 1e9:.1f} GB)"},
            "roofline": {"kernel": "k_march_f32c", "bound": "hbm", "achieved": ach, "peak": peaks.get("hbm_gbs"),
                         "unit": "GB/s", "frac": ach / peaks.get("hbm_gbs", 6800.0), "traffic": None,
                         "bytes_per_update": 16, "launch_ms": t_march, "peak_source": src},

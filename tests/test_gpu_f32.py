@@ -151,3 +151,29 @@ def test_autotune_and_plan_knobs(F, oracle, tmp_path):
     ch = A.tune(cfgs, rows=128, candidates=cand, cache_path=str(tmp_path / "tune.json"))
     print("autotune table (cluster CTAs, mid weight, ms):", ch.table)
     assert (ch.cluster_ctas, ch.mid_weight) in cand and all(t[2] > 0 for t in ch.table)
+
+
+def test_wait_timeout_latches_status(F):
+    # a wait limit of one cycle: the first band or warp that has to wait for another
+    # (band c-1's inner pass or last row, the warp above's queue) gives up at once,
+    # latches FDTD_ERR_TIMEOUT and marches on without waiting; every later wait sees
+    # the status and returns, so the launch ends.  The readout reports the status,
+    # and a fresh plan with the default limit marches normally on the same context
+    import ctypes
+    import torch
+    ws = [W.exp_pair(4096, 1100, D=40), W.exp_pair(900, 500, D=12)]
+    arr = (F.FdtdParams * len(ws))(*[cparams(F, w, tstep=-1, cluster_ctas=4, spin_cycles=1) for w in ws])
+    L = F.lib()
+    nb, plan = ctypes.c_size_t(), ctypes.c_void_p()
+    assert L.fdtd_plan(arr, len(ws), None, ctypes.byref(nb), ctypes.byref(plan)) == F.OK
+    buf = torch.empty(nb.value + 256, dtype=torch.uint8, device="cuda")
+    F.fdtd_bind_workspace(plan, (buf.data_ptr() + 255) // 256 * 256, nb.value)
+    F.fdtd_set_boundary(plan)
+    F.fdtd_march(plan, max(w.nt for w in ws))
+    norms = np.empty(ws[0].nt, dtype=np.float64)
+    st = L.fdtd_readout_instance(plan, 0, F.READ_NORMS, ctypes.c_void_p(norms.ctypes.data), norms.nbytes)
+    assert st == F.ERR_TIMEOUT
+    F.fdtd_destroy(plan)
+    del buf
+    (snaps, norms), = run_batch(F, [W.exp_pair(1024, 600, D=40)])
+    assert np.all(np.isfinite(snaps)) and np.all(np.isfinite(norms))
