@@ -215,10 +215,16 @@ __global__ void __launch_bounds__(kMarchThreads, 1) k_march_f64(const MarchArgs 
   const int64_t G2 = (2 * (int64_t)D < A.nx) ? 2 * (int64_t)D : A.nx;
   int64_t s0, s1;
   if (j_lo >= G2) {
-    const int64_t seg = ((j_hi - j_lo + kMarchThreads - 1) / kMarchThreads) | 1;
-    s0 = j_lo + (int64_t)tid * seg;
+    // odd lengths; warp 0, which also waits on the neighbours and forms the halo carry,
+    // takes 2 columns fewer
+    const int64_t len = j_hi - j_lo;
+    int64_t seg = ((len + 64 + kMarchThreads - 1) / kMarchThreads) | 1;
+    if (seg < 3) seg = 3;
+    const int64_t seg0 = seg - 2;
+    s0 = (tid < 32) ? j_lo + (int64_t)tid * seg0 : j_lo + 32 * seg0 + (int64_t)(tid - 32) * seg;
     if (s0 > j_hi) s0 = j_hi;
-    s1 = (s0 + seg < j_hi) ? s0 + seg : j_hi;
+    const int64_t sl = (tid < 32) ? seg0 : seg;
+    s1 = (s0 + sl < j_hi) ? s0 + sl : j_hi;
   } else {
     const int64_t wm = A.mid_weight;
     auto cumw = [&](int64_t j) { return j <= G2 ? wm * j : wm * G2 + (j - G2); };
