@@ -204,7 +204,8 @@ def main():
                     help="large/small workloads: the double-float march (default) or the FP64 march; both are "
                          "held to the same 1e-12 parity with the FP64 oracle")
     ap.add_argument("--no-variants", action="store_true", help="large workload: skip the variants object")
-    ap.add_argument("--variant-rows", type=int, default=8193, help="rows of the FP64-march variant")
+    ap.add_argument("--variant-rows", type=int, default=8193,
+                    help="rows of the FP64-march variant, timed after its first launch")
     ap.add_argument("--ref-rows", type=int, default=4096)
     ap.add_argument("--cpu-rows", type=int, default=6144)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -619,14 +620,16 @@ def surrogate_variant(args, steps, warmup, peaks, src):
 
 
 def f64_variant(args, rows, alu_fp64):
-    """The native FP64 march (FDTD_F64, k_march_f64) on the first `rows` rows of the
-    large workload, in the default launch size: one untimed pass, one timed pass
-    with CUDA events around every launch on the plan's stream."""
+    """The native FP64 march (FDTD_F64, k_march_f64) on `rows` - 1 rows of the large
+    workload after its first launch (rows 1 .. rows_per_launch, untimed, take the march
+    past the delay onset at row D + 1: earlier rows skip the delay term and are cheaper),
+    in the default launch size: one untimed pass, one timed pass with CUDA events around
+    every launch on the plan's stream."""
     import torch
 
     from paper_1707_05943_gb300 import fdtd as F
-    w = W.LARGE.with_(nt=rows)
     rpl = args.rows_per_launch
+    w = W.LARGE.with_(nt=rows + rpl)
     stream = torch.cuda.Stream()
     cfg = F.Config(nx=w.nx, nt=w.nt, D=w.D, delta=w.delta, gamma=w.gamma, omega0=w.omega0, k=w.k,
                    init_cond=w.init_cond, alpha=w.alpha, sigma=w.sigma, center=w.center, tstep=-1,
@@ -636,7 +639,8 @@ def f64_variant(args, rows, alu_fp64):
 
     def step(record):
         s.set_boundary()
-        done = 1
+        s.march(rpl)
+        done = 1 + rpl
         while done < w.nt:
             n = min(rpl, w.nt - done)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -662,7 +666,7 @@ def f64_variant(args, rows, alu_fp64):
     s.close()
     del s
     return {"value": upd / (ms * 1e-3), "unit": UNIT, "dtype": "f64", "kernel": "k_march_f64",
-            "rows_measured": rows - 1, "march_ms": ms, "launch_ms": launch_ms,
+            "rows_measured": rows - 1, "rows_from": rpl + 1, "march_ms": ms, "launch_ms": launch_ms,
             "roofline": {"bound": "alu", "achieved": ach, "peak": alu_fp64, "unit": "TFLOP/s",
                          "frac": ach / alu_fp64, "flops_per_update": FLOPS_PER_UPDATE_F64,
                          "peak_source": "measured in this run (fdtd_alu_probe, FP64 FMA)"},

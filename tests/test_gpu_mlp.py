@@ -10,7 +10,7 @@ Forward and gradient: the reference uses the same BF16-rounded weights in
 FP64; the kernels also round every hidden activation and every backpropagated
 signal to BF16 (relative 2^-9 each, about 1e-3 after averaging over many
 terms); measured 1.5e-3 (forward) and 1.6e-4 to 1.8e-3 (gradients) on these
-seeded inputs, 5e-3 allowed.  Adam: FP32
+seeded inputs, 3e-3 allowed.  Adam: FP32
 arithmetic of one update, 1e-5 of the learning rate.
 """
 import ctypes
@@ -134,7 +134,7 @@ def test_forward_matches_fp64_reference(env):
     want, _, _ = R.forward(net.theta_eff(), DIMS_SMALL, x.astype(np.float64))
     err = np.linalg.norm(got - want) / np.linalg.norm(want)
     print(f"forward rel L2 vs FP64 reference: {err:.3e}")
-    assert err < 5e-3
+    assert err < 3e-3
 
 
 def test_gradient_matches_fp64_reference(env):
@@ -160,7 +160,7 @@ def test_gradient_matches_fp64_reference(env):
             g, w = got[o:o + size], want[o:o + size]
             err = np.linalg.norm(g - w) / np.linalg.norm(w)
             print(f"layer {l} d{name}: rel L2 {err:.3e}")
-            assert err < 5e-3, (l, name, err)
+            assert err < 3e-3, (l, name, err)
             o += size
 
 
