@@ -53,11 +53,12 @@ UNIT = "grid-point updates/s"
 BYTES_PER_UPDATE_F64 = 32
 FLOPS_PER_UPDATE_F64 = 46
 # double-float march (k_march_dw), per bulk update: FP32-pipe instructions (FADD, FMUL, FFMA
-# each 1) and flops (FMA = 2), counted from its source: 5 complex double-float products of
-# the right-hand side, 3 sums, the recurrence step and renormalisation, the norm term, and
-# the carry correction on ~6 of every 15 columns
-DW_FP32_INSTR_PER_UPDATE = 376
-DW_FLOPS_PER_UPDATE = 460
+# each 1) and flops (FMA = 2), counted from its source: the complex double-float products
+# d1 a (32 instructions), c3 (delay square), R1 detab, R2 phi and c2 (b + y) (48 each), four
+# sums (16 each), the renormalisation (4), the norm term (24), and the carry correction on
+# about 6 of every 15 columns (28)
+DW_FP32_INSTR_PER_UPDATE = 344
+DW_FLOPS_PER_UPDATE = 416
 
 
 def env_rank():
@@ -328,8 +329,8 @@ def main():
                                   "scaled to this launch's updates",
                 "hbm": hbm}
     else:
-        # FP32-pipe work of a bulk update of the double-float march, from ncu's executed
-        # FADD/FMUL/FFMA counts of k_march_dw over one launch (see DW_* constants)
+        # FP32-pipe work of a bulk update of the double-float march, counted from its
+        # source (see DW_* constants)
         ach = DW_FP32_INSTR_PER_UPDATE * upd_launch / (avg_ms * 1e-3) / 1e12
         pk = alu_peaks["fp32"] / 2  # FMA rate = FP32 pipe instruction rate
         roof = {"kernel": "k_march_dw", "bound": "alu", "achieved": ach, "peak": pk,

@@ -287,6 +287,11 @@ __device__ __forceinline__ zc step_dw(const DwArgs& A, zc r, const zc& y) {
   cmac(r, zc_of(A.c2), y);
   return cnorm(r);
 }
+// the same with r_j's c2 b_j term still out: y_j = c2 (b_j + y_{j-1}) + r'_j (one product)
+__device__ __forceinline__ zc step_b_dw(const DwArgs& A, zc r, const zc& b, const zc& y) {
+  cmac(r, zc_of(A.c2), cadd(b, y));
+  return cnorm(r);
+}
 
 __device__ __forceinline__ void finalize_dw(const DwArgs& A, const RowDw& R, int64_t j, const zc& y, float& nh,
                                             float& nl) {
@@ -421,7 +426,8 @@ __global__ void __launch_bounds__(kDwThreads, kDwCtasPerSm) k_march_dw(const DwA
       zc hp_n = use_hs ? zc_of(bh[0]) : zc0();
       zc E_n = (kE >= 0) ? ldz_ro(bE) : zc0();
       zc F_n = (kF >= 0) ? ldz_ro(bF) : zc0();
-      auto col = [&](int k) -> zc {  // r of column s0 + k from the values loaded for it; loads for k + 1
+      zc bcur = zc0();  // b of the column col() formed last
+      auto col = [&](int k) -> zc {  // r' of column s0 + k (no c2 b) from the values loaded for it; loads for k + 1
         const zc b = b_n, pD = pD_n, pD1 = pD1_n, hpv = hp_n, E = E_n, Fv = F_n;
         const int k1 = k + 1;
         if (k1 < len) {
@@ -432,8 +438,7 @@ __global__ void __launch_bounds__(kDwThreads, kDwCtasPerSm) k_march_dw(const DwA
           E_n = (k1 <= kE) ? ldz_ro(bE - k1) : zc0();
           F_n = (k1 <= kF) ? ldz_ro(bF - k1) : zc0();
         }
-        zc S = cmul(zc_of(A.d1), a);
-        cmac(S, zc_of(A.c2), b);
+        zc S = cmul(zc_of(A.d1), a);  // c2 b enters with c2 y in the step: c2 (b + y)
         if (dd) {
           const zc hn = cadd(pDp, pD);  // row n-D pair
           if (dd1) cmac(S, zc_of(A.c3), cadd(hn, use_hs ? hpv : cadd(pD1p, pD1)));
@@ -444,6 +449,7 @@ __global__ void __launch_bounds__(kDwThreads, kDwCtasPerSm) k_march_dw(const DwA
           if (k <= kF) cmac(S, R.R2, Fv);
         }
         const zc r = cadd(a, S);
+        bcur = b;
         a = b;
         pDp = pD;
         pD1p = pD1;
@@ -451,12 +457,16 @@ __global__ void __launch_bounds__(kDwThreads, kDwCtasPerSm) k_march_dw(const DwA
       };
 #pragma unroll
       for (int v = 0; v < P; ++v) {
-        if (v < len) y = step_dw(A, col(v), y);
+        if (v < len) {
+          const zc r = col(v);
+          y = step_b_dw(A, r, bcur, y);
+        }
         y0[v] = y;
       }
       float4* o = R.row0 + s0;
       for (int k = P; k < len; ++k) {
-        y = step_dw(A, col(k), y);
+        const zc r = col(k);
+        y = step_b_dw(A, r, bcur, y);
         if (k < A.kfix) stz(o + k, y);  // provisional: receives the carry in pass B
         else finalize_dw(A, R, s0 + k, y, nh_, nl_);
       }
