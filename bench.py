@@ -46,19 +46,49 @@ import workloads as W  # noqa: E402
 
 METRIC = "grid-point updates/s & % HBM peak; FP32/batched vs plain FP64 at stated error"
 UNIT = "grid-point updates/s"
-# algorithmic work per update of the FP64 bulk (x > 3a), as the kernel computes it:
-#   bytes: one delay value read from HBM + one value written = 2 x 16 B
-#   flops: c1 a (6) + delay 4-sum (6) x c3 (6+2) + sources R1 detab, R2 phi (2 x 8)
-#          + y_{m-1} + b (2) + c2 (y_{m-1} + b) (6+2) = 46
-BYTES_PER_UPDATE_F64 = 32
-FLOPS_PER_UPDATE_F64 = 46
-# double-float march (k_march_dw), per bulk update: FP32-pipe instructions (FADD, FMUL, FFMA
-# each 1) and flops (FMA = 2), counted from its source: the complex double-float products
-# d1 a (32 instructions), c3 (delay square), R1 detab, R2 phi and c2 (b + y) (48 each), four
-# sums (16 each), the renormalisation (4), the norm term (24), and the carry correction on
-# about 6 of every 15 columns (28)
-DW_FP32_INSTR_PER_UPDATE = 344
-DW_FLOPS_PER_UPDATE = 416
+# algorithmic work of the march, per update of x > 3a, split by the terms an update
+# carries (the kernels compute exactly these):
+#   always: c1 a, the recurrence step y = c2 (y + b) + q, the row norm term
+#   rows n >= D + 1: the delay square (pair sums of rows n-D, n-D-1) times c3
+#   the sources act only inside the light cone of the boundary: R1 dE for j <= n + D - 1,
+#   R2 phi for j <= n - 1 (columns beyond are skipped by the kernels: nothing has arrived)
+# bytes: the value written (16 B) and, for rows n >= D, the delay value read (16 B); row
+# n-1 and the pair sums of row n-D-1 come from L2 and shared memory.
+# FP64 (k_march_f64), FP64-pipe instructions (DADD, DMUL, DFMA each 1) and flops (FMA = 2):
+# base: c1 a (2 DMUL + 2 DFMA, 6 flops), y + b (2 DADD), c2 (y + b) + q (4 DFMA, 8), the norm
+# term (2 DFMA, 4) = 12 instructions, 20 flops; delay: the row n-D pair sum (2 DADD; it is
+# the next row's n-D-1 pair, kept in shared memory), + the n-D-1 pair (2 DADD), c3 times
+# that, accumulated (4 DFMA) = 8 instructions, 12 flops; each source product accumulated
+# (4 DFMA) = 4 instructions, 8 flops.
+F64_INSTR = {"base": 12, "delay": 8, "src": 4}
+F64_FLOPS = {"base": 20, "delay": 12, "src": 8}
+# double-float (k_march_dw), FP32-pipe instructions (FADD, FMUL, FFMA each 1) and flops
+# (FMA = 2) of its operations: complex double-float product into a fresh value (cmul, 32
+# instructions, 44 flops), product accumulated (cmac, 48, 60), sum (cadd, 16, 16),
+# renormalisation (6, 6), norm term (24, 28).  base: d1 a cmul + a + S + b + y + c2 cmac +
+# renormalisation + norm = 142 instructions (170 flops); delay: two pair sums + c3 cmac =
+# 80 (92); each source: one cmac = 48 (60).  The carry correction of the parallel row scan
+# is not counted (a sequential march does not need it).
+DW_INSTR = {"base": 142, "delay": 80, "src": 48}
+DW_FLOPS = {"base": 170, "delay": 92, "src": 60}
+
+
+def march_work(w, n0: int, n1: int) -> dict:
+    """Exact counts over rows n0 .. n1-1 of the march of workload w: updates, updates with
+    the delay term (rows n >= D + 1), updates with each boundary source (bulk columns
+    2D <= j <= n + D - 1 for R1 dE, 2D <= j <= n - 1 for R2 phi), and algorithmic HBM bytes."""
+    import numpy as np
+    n = np.arange(n0, n1, dtype=np.int64)
+    g2 = min(2 * w.D, w.nx)
+    upd = (n1 - n0) * w.nx
+    dly = int(np.count_nonzero(n >= w.D + 1)) * w.nx
+    src = int(np.clip(np.minimum(w.nx, n + w.D) - g2, 0, None).sum() + np.clip(np.minimum(w.nx, n) - g2, 0, None).sum())
+    nbytes = 16 * upd + 16 * int(np.count_nonzero(n >= w.D)) * w.nx
+    return {"updates": upd, "delay": dly, "src": src, "bytes": nbytes}
+
+
+def work_of(counts: dict, table: dict) -> float:
+    return table["base"] * counts["updates"] + table["delay"] * counts["delay"] + table["src"] * counts["src"]
 
 
 def env_rank():
@@ -265,7 +295,7 @@ def main():
                 e0.record(stream)
                 solver.march(n)
                 e1.record(stream)
-                events.append((e0, e1, n))
+                events.append((e0, e1, n, done))
             else:
                 solver.march(n)
             done += n
@@ -304,40 +334,48 @@ def main():
     updates_per_step = w.updates
     value = job_value(updates_per_step, args.steps, world, ms * 1e-3)
 
-    # dominant kernel: the march launches (full-size ones)
-    full = [(a.elapsed_time(b), n) for a, b, n in events if n == rpl] or [(a.elapsed_time(b), n) for a, b, n in events]
-    avg_ms = sum(t for t, _ in full) / len(full)
-    rows_l = full[0][1]
+    # dominant kernel: the march launches (full-size ones); the algorithmic work of each
+    # launch is counted exactly over its rows (the light cone makes later rows dearer)
+    full = [e for e in events if e[2] == rpl] or list(events)
+    t_full = sum(a.elapsed_time(b) for a, b, _, _ in full)
+    avg_ms = t_full / len(full)
+    rows_l = full[0][2]
     peaks, src = load_peaks()
     upd_launch = rows_l * w.nx
-    ach_gbs = BYTES_PER_UPDATE_F64 * upd_launch / (avg_ms * 1e-3) / 1e9
+    cnt = {"updates": 0, "delay": 0, "src": 0, "bytes": 0}
+    for _, _, n, n0 in full:
+        for k, v in march_work(w, n0, n0 + n).items():
+            cnt[k] += v
+    sec = t_full * 1e-3
+    ach_gbs = cnt["bytes"] / sec / 1e9
     hbm = {"achieved": ach_gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-           "frac": ach_gbs / peaks.get("hbm_gbs", 6800.0), "bytes_per_update": BYTES_PER_UPDATE_F64,
+           "frac": ach_gbs / peaks.get("hbm_gbs", 6800.0), "bytes_per_update": cnt["bytes"] / cnt["updates"],
            "peak_source": src}
+    work = {"updates": cnt["updates"], "with_delay": cnt["delay"], "source_products": cnt["src"],
+            "launches": len(full)}
     if prec == fdtd.F64:
-        # DRAM bytes per update from one ncu capture of k_march_f64 (2^20 columns, D = 100, 4096 rows:
-        # 137.9 GB per launch); the D = 2000 launch moves the same bytes per update (both delay rows
-        # lie far outside L2), so the figure is scaled by the updates of one launch
-        ach = FLOPS_PER_UPDATE_F64 * upd_launch / (avg_ms * 1e-3) / 1e12
-        roof = {"kernel": "k_march_f64", "bound": "alu", "achieved": ach, "peak": alu_peaks["fp64"],
-                "unit": "TFLOP/s", "frac": ach / alu_peaks["fp64"],
+        ins, fl = work_of(cnt, F64_INSTR), work_of(cnt, F64_FLOPS)
+        ach = ins / sec / 1e12
+        pk = alu_peaks["fp64"] / 2  # DFMA rate = FP64 pipe instruction rate
+        roof = {"kernel": "k_march_f64", "bound": "alu", "achieved": ach, "peak": pk,
+                "unit": "T FP64-pipe instructions/s (DADD, DMUL, DFMA each 1)", "frac": ach / pk,
                 "peak_source": "measured in this run: FP64 FMA throughput of fdtd_alu_probe (independent "
-                               "FMA chains on every SM, CUDA events)",
-                "flops_per_update": FLOPS_PER_UPDATE_F64, "updates_per_launch": upd_launch, "launch_ms": avg_ms,
-                "traffic": 32.1 * upd_launch,
+                               "FMA chains on every SM, CUDA events) / 2 flops per FMA",
+                "fp64_instr_per_update": ins / cnt["updates"], "flops_per_update": fl / cnt["updates"],
+                "flops_frac": fl / sec / 1e12 / alu_peaks["fp64"], "work": work, "updates_per_launch": upd_launch,
+                "launch_ms": avg_ms, "traffic": 32.1 * upd_launch,
                 "traffic_source": "ncu dram__bytes_read+write of k_march_f64 at nx 2^20, D 100 (32.1 B/update), "
                                   "scaled to this launch's updates",
                 "hbm": hbm}
     else:
-        # FP32-pipe work of a bulk update of the double-float march, counted from its
-        # source (see DW_* constants)
-        ach = DW_FP32_INSTR_PER_UPDATE * upd_launch / (avg_ms * 1e-3) / 1e12
+        ins, fl = work_of(cnt, DW_INSTR), work_of(cnt, DW_FLOPS)
+        ach = ins / sec / 1e12
         pk = alu_peaks["fp32"] / 2  # FMA rate = FP32 pipe instruction rate
         roof = {"kernel": "k_march_dw", "bound": "alu", "achieved": ach, "peak": pk,
                 "unit": "T FP32-pipe instructions/s (FADD, FMUL, FFMA each 1)", "frac": ach / pk,
                 "peak_source": "measured in this run: FP32 FMA throughput of fdtd_alu_probe / 2 flops per FMA",
-                "fp32_instr_per_update": DW_FP32_INSTR_PER_UPDATE, "flops_per_update": DW_FLOPS_PER_UPDATE,
-                "flops_frac": DW_FLOPS_PER_UPDATE * upd_launch / (avg_ms * 1e-3) / alu_peaks["fp32"],
+                "fp32_instr_per_update": ins / cnt["updates"], "flops_per_update": fl / cnt["updates"],
+                "flops_frac": fl / sec / 1e12 / alu_peaks["fp32"], "work": work,
                 "updates_per_launch": upd_launch, "launch_ms": avg_ms, "traffic": None,
                 "traffic_source": "no ncu capture of this kernel at this size yet", "hbm": hbm}
 
@@ -659,15 +697,21 @@ def f64_variant(args, rows, alu_fp64):
     upd = w.nx * sum(n for _, _, n in ev)
     full = [a.elapsed_time(b) for a, b, n in ev if n == rpl] or [ms]
     launch_ms = sum(full) / len(full)
-    ach = FLOPS_PER_UPDATE_F64 * rpl * w.nx / (launch_ms * 1e-3) / 1e12
+    cnt = march_work(w, pre + 1, w.nt)
+    ins, fl = work_of(cnt, F64_INSTR), work_of(cnt, F64_FLOPS)
+    ach = ins / (ms * 1e-3) / 1e12
     s.close()
     del s
     return {"value": upd / (ms * 1e-3), "unit": UNIT, "dtype": "f64", "kernel": "k_march_f64",
             "rows_measured": rows - 1, "rows_from": pre + 1, "march_ms": ms, "launch_ms": launch_ms,
-            "roofline": {"bound": "alu", "achieved": ach, "peak": alu_fp64, "unit": "TFLOP/s",
-                         "frac": ach / alu_fp64, "flops_per_update": FLOPS_PER_UPDATE_F64,
-                         "peak_source": "measured in this run (fdtd_alu_probe, FP64 FMA)"},
-            "how": f"march only, first {rows} rows of {W.LARGE.name}, CUDA events per launch", "clocks": clocks}
+            "roofline": {"bound": "alu", "achieved": ach, "peak": alu_fp64 / 2,
+                         "unit": "T FP64-pipe instructions/s (DADD, DMUL, DFMA each 1)",
+                         "frac": ach / (alu_fp64 / 2), "fp64_instr_per_update": ins / cnt["updates"],
+                         "flops_per_update": fl / cnt["updates"],
+                         "flops_frac": fl / (ms * 1e-3) / 1e12 / alu_fp64,
+                         "peak_source": "measured in this run (fdtd_alu_probe, FP64 FMA) / 2 flops per FMA"},
+            "how": f"march only, rows {pre + 1}..{w.nt - 1} of {W.LARGE.name} (rows 1..{pre} marched untimed first), "
+                   "CUDA events per launch", "clocks": clocks}
 
 
 def solver_grid(s) -> int:
