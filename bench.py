@@ -376,7 +376,9 @@ def main():
                 "peak_source": "measured in this run: FP32 FMA throughput of fdtd_alu_probe / 2 flops per FMA",
                 "fp32_instr_per_update": ins / cnt["updates"], "flops_per_update": fl / cnt["updates"],
                 "flops_frac": fl / sec / 1e12 / alu_peaks["fp32"], "work": work,
-                "updates_per_launch": upd_launch, "launch_ms": avg_ms, "traffic": None,
+                "updates_per_launch": upd_launch, "launch_ms": avg_ms,
+                "launch_ms_each": [round(a.elapsed_time(b), 2) for a, b, n, _ in events[:len(events) // max(args.steps, 1)]],
+                "traffic": None,
                 "traffic_source": "no ncu capture of this kernel at this size yet", "hbm": hbm}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
